@@ -1,0 +1,109 @@
+"""Pins of the oracle's method-of-lines stepping (Section 4.2, Section 6,
+Section 7): BiCGSTAB against a dense direct solve, SBDF2 against the
+closed-form recurrence of a scalar linear test problem, fixed points of the
+kinetics, exact heat-equation decay of a spherical harmonic, and the
+iteration counts Section 6 reports."""
+import json
+import cmath
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import operator as oop
+from oracle import stepping as ostp
+from oracle import weights as ow
+from paper_1404_0812_gb300 import workloads as W
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+@pytest.fixture(scope="module")
+def op642():
+    ns = W.icosahedral_sphere(3)
+    return ns, oop.build_operator(ns.X, ns.normals, 31, ow.GAUSSIAN, kappa_T=1e12)
+
+
+def test_bicgstab_matches_dense_solve(op642):
+    ns, op = op642
+    L = oop.dense(op, ns.N)
+    A = 3.0 * np.eye(ns.N) - 2 * 0.05 * L
+    b = W.uniform_field(ns.N, seed=11)
+    x, it, rel, ok = ostp.bicgstab(lambda v: A @ v, b, np.zeros(ns.N), 1e-13, 500)
+    assert ok and rel <= 1e-13
+    xd = np.linalg.solve(A, b)
+    assert np.abs(x - xd).max() <= 1e-11 * np.abs(xd).max()
+
+
+def _sbdf2_closed_form(lam, mu, dt, u0, n):
+    """Scalar problem u' = -lam u + mu u (L = -I, diffusion lam): step 1 is
+    IMEX Euler, then (3 + 2 lam dt) u+ = (4 + 4 mu dt) u - (1 + 2 mu dt) u-,
+    whose solution is A r1^n + B r2^n with r the roots of the characteristic
+    quadratic."""
+    u1 = (1.0 + dt * mu) * u0 / (1.0 + dt * lam)
+    a, b, cc = 3.0 + 2.0 * lam * dt, -(4.0 + 4.0 * mu * dt), 1.0 + 2.0 * mu * dt
+    disc = cmath.sqrt(b * b - 4 * a * cc)
+    r1, r2 = (-b + disc) / (2 * a), (-b - disc) / (2 * a)
+    B = (u1 - r1 * u0) / (r2 - r1)
+    A = u0 - B
+    return (A * r1 ** n + B * r2 ** n).real
+
+
+def test_sbdf2_recurrence_closed_form():
+    lam, mu, dt = 7.0, 0.6, 0.05
+    p = dict(model="linear", lu=mu, lv=-mu, dt=dt, delta_u=1.0, delta_v=2.0)
+    u0 = np.array([1.0, -0.5, 2.0])
+    v0 = np.array([0.3, 0.1, -1.0])
+    out = ostp.imex_run(lambda x: -lam * x, u0, v0, p, 40, tol=1e-14)
+    ref_u = _sbdf2_closed_form(lam * 1.0, mu, dt, 1.0, 40)
+    ref_v = _sbdf2_closed_form(lam * 2.0, -mu, dt, 1.0, 40)
+    np.testing.assert_allclose(out["u"], u0 * ref_u, rtol=1e-12)
+    np.testing.assert_allclose(out["v"], v0 * ref_v, rtol=1e-12)
+
+
+def test_kinetics_fixed_points():
+    # Section 7: with alpha = -gamma, (0, 0) is an equilibrium; the linear part
+    # of Eqs. turing1/turing2 at the origin is [[alpha, 1], [gamma, beta]].
+    row = GOLDEN["turing_table"]["rows"][0]
+    p = dict(model="barrio", **{k: row[k] for k in ("alpha", "beta", "gamma", "tau1", "tau2")})
+    assert p["alpha"] == -p["gamma"]
+    z = np.zeros(1)
+    f, g = ostp.reaction(p, z, z)
+    assert f[0] == 0.0 and g[0] == 0.0
+    h = 1e-7
+    fu, gu = ostp.reaction(p, z + h, z)
+    fv, gv = ostp.reaction(p, z, z + h)
+    J = np.array([[fu[0], fv[0]], [gu[0], gv[0]]]) / h
+    np.testing.assert_allclose(J, [[p["alpha"], 1.0], [p["gamma"], p["beta"]]], atol=1e-6)
+    assert W.BARRIO_SPOTS["delta_u"] == pytest.approx(
+        GOLDEN["turing_table"]["delta_u_over_delta_v"] * W.BARRIO_SPOTS["delta_v"])
+    s = W.SCHNAKENBERG
+    us, vs = s["a"] + s["b"], s["b"] / (s["a"] + s["b"]) ** 2
+    f, g = ostp.reaction(s, np.array([us]), np.array([vs]))
+    assert abs(f[0]) < 1e-15 and abs(g[0]) < 1e-15
+    f, g = ostp.reaction(W.GRAY_SCOTT, np.ones(1), np.zeros(1))
+    assert f[0] == 0.0 and g[0] == 0.0
+
+
+def test_steady_state_stays_constant(op642):
+    ns, op = op642
+    s = W.SCHNAKENBERG
+    u = np.full(ns.N, s["a"] + s["b"])
+    v = np.full(ns.N, s["b"] / (s["a"] + s["b"]) ** 2)
+    out = ostp.imex_run(lambda x: oop.apply(op, x), u, v, s, 5)
+    assert np.abs(out["u"] - u).max() < 1e-10 and np.abs(out["v"] - v).max() < 1e-10
+
+
+def test_heat_equation_decay_and_iteration_count(op642):
+    """u0 = Y_3^2 decays as exp(-12 t) (Section 6 series with l = 3); at
+    dt = 1e-4 BiCGSTAB needs at most three iterations per step to a relative
+    tolerance of 1e-12 (Section 6)."""
+    ns, op = op642
+    g = GOLDEN["bicgstab_bdf"]
+    u0 = W.sph_harm_y32(ns.X)
+    p = dict(model="none", dt=g["dt"], delta_u=1.0)
+    out = ostp.imex_run(lambda x: oop.apply(op, x), u0, None, p, 100, tol=g["tol"])
+    err = np.abs(out["u"] - math.exp(-12 * 0.01) * u0).max() / np.abs(u0).max()
+    assert err < 2e-5
+    assert max(i for i, _ in out["iters"]) <= g["max_iters"]
