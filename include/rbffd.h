@@ -1,0 +1,262 @@
+/*
+ * rbffd.h - C ABI of the GB300 (sm_103a) RBF-FD surface Laplace-Beltrami
+ * library: batched per-stencil operator build with a per-stencil shape
+ * parameter, fixed-width (sliced ELL) application, and IMEX (SBDF2 +
+ * BiCGSTAB) reaction-diffusion stepping.
+ *
+ * Method: Shankar, Wright, Kirby, Fogelson, "A Radial Basis Function
+ * (RBF)-Finite Difference (FD) Method for Diffusion and Reaction-Diffusion
+ * Equations on Surfaces".  Each entry point cites the section / equation
+ * that defines what it computes.
+ *
+ * Conventions for every call:
+ *  - Pointers marked "device" are CUDA device pointers on the current
+ *    device; "host" pointers are ordinary host memory.  Arrays are dense and
+ *    C-contiguous.  Node coordinates and normals are N x 3 row-major float64.
+ *  - The caller owns every buffer it passes; the library owns what it
+ *    allocates inside an rbffd_op / rbffd_mlp until the matching destroy.
+ *  - Work is queued on the given stream (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream).  Calls that return data to host
+ *    memory or a status depending on device results synchronise that stream.
+ *  - Nothing throws across the ABI: every call returns an rbffd_status, and
+ *    rbffd_last_error() gives a one-line message for the last failure on the
+ *    calling thread.
+ */
+#ifndef RBFFD_H
+#define RBFFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RBFFD_OK = 0,
+    RBFFD_EINVAL = 1,                 /* bad argument (size, pointer, option) */
+    RBFFD_ECUDA = 2,                  /* a CUDA runtime call failed */
+    RBFFD_ENOMEM = 3,                 /* device allocation failed */
+    RBFFD_EPS_SEARCH_FAILED = 4,      /* some stencil's eps search found no root */
+    RBFFD_SOLVER_NOT_CONVERGED = 5,   /* BiCGSTAB hit its cap or broke down */
+    RBFFD_TIMEOUT = 6,                /* a bounded device-side wait gave up */
+    RBFFD_NOT_IMPLEMENTED = 7,
+    RBFFD_ESINGULAR = 8               /* a local interpolation matrix is not
+                                         numerically positive definite */
+} rbffd_status;
+
+enum { RBFFD_GAUSSIAN = 0, RBFFD_IMQ = 1 };   /* Section 2 kernels */
+enum { RBFFD_F32 = 0, RBFFD_F64 = 1 };        /* stepping / apply precision */
+enum { RBFFD_MAX_GROUPS = 8, RBFFD_MAX_N = 128 };
+
+/* Per-stencil status codes written by the build (rbffd_get_stencil_info). */
+enum { RBFFD_STENCIL_OK = 0, RBFFD_STENCIL_NO_BRACKET = 1,
+       RBFFD_STENCIL_NO_CONVERGENCE = 2, RBFFD_STENCIL_SINGULAR = 3,
+       RBFFD_STENCIL_ACCEPTED_PREDICTION = 4 };
+
+typedef struct rbffd_op rbffd_op;     /* opaque, library-owned operator */
+typedef struct rbffd_mlp rbffd_mlp;   /* opaque, library-owned eps network */
+
+/* Options of rbffd_build_operator. */
+typedef struct {
+    int kernel;               /* RBFFD_GAUSSIAN or RBFFD_IMQ (Section 2) */
+    double kappa_target;      /* kappa_T of Eq. target_cond (> 1) */
+    double eps_tol;           /* absolute tolerance on eps (Section 5: 1e-4) */
+    int max_evals;            /* cap on kappa evaluations per stencil (e.g. 64) */
+    int use_learned;          /* 1: first guess from the network in mlp[] whose
+                                 stencil size matches the row's n */
+    double accept_lo;         /* accept the prediction when kappa(A(eps_hat)) */
+    double accept_hi;         /*   lies in [accept_lo, accept_hi] * kappa_T */
+    const double* eps_override; /* device, N, or NULL: fixed eps per node (no
+                                   search; kappa/evals reported as NaN/0) */
+    const rbffd_mlp* mlp[RBFFD_MAX_GROUPS]; /* learned networks (may be NULL) */
+    int block_threads;        /* 0 = autotuned / default launch shape */
+    int blocks_per_sm;        /* 0 = autotuned / default launch shape */
+} rbffd_build_opts;
+
+/* Fill opts with defaults: IMQ, kappa_T 1e12, eps_tol 1e-4, max_evals 64,
+ * no learned start, band [0.5, 2]. */
+void rbffd_build_opts_default(rbffd_build_opts* opts);
+
+/*
+ * rbffd_build_operator - the discrete surface Laplacian L_X (Section 4).
+ *
+ * For every node k: its stencil P_k (k first, then its n_k - 1 nearest other
+ * nodes by Euclidean distance in R^3, ties broken by node index; Section 4,
+ * Section 4.1), a shape parameter eps_k (the zero of
+ * F(eps) = ln(kappa_2(A_{P_k}(eps)) / kappa_T), Eq. target_cond, searched to
+ * opts->eps_tol; Section 5) and the weights: the first row of
+ * L_P = G^x G^x + G^y G^y + G^z G^z, G^d = B^d A^{-1} (Eqs. proj_mat,
+ * grad_x_f_interp, surface_lap_P1).  All local linear algebra is float64.
+ *
+ *   nodes      device, N x 3 float64, distinct points on the surface
+ *   normals    device, N x 3 float64, unit normals (sign irrelevant)
+ *   N          number of nodes (>= 2)
+ *   n_per_node device int32 N (stencil size of each node, 2..128, at most 8
+ *              distinct values) or NULL to use n_uniform for every node
+ *   opts       options (NULL = defaults)
+ *   stream     cudaStream_t (void*)
+ *   out        receives the new operator (NULL on failure)
+ *
+ * Returns RBFFD_OK, RBFFD_EINVAL (bad sizes / options), RBFFD_ENOMEM,
+ * RBFFD_ECUDA, or RBFFD_EPS_SEARCH_FAILED / RBFFD_ESINGULAR when at least one
+ * stencil failed (the operator is still returned; per-stencil status is in
+ * rbffd_get_stencil_info).  Synchronises the stream.
+ */
+rbffd_status rbffd_build_operator(const double* nodes, const double* normals, int64_t N,
+                                  const int32_t* n_per_node, int n_uniform,
+                                  const rbffd_build_opts* opts, void* stream,
+                                  rbffd_op** out);
+
+/*
+ * rbffd_apply - y = L_X u (Eq. kernel_mol, explicit part; Section 4.2).
+ *   u, y   device, N values of dtype (RBFFD_F32 uses the float32 copy of the
+ *          weights, RBFFD_F64 the float64 weights); u and y must not alias.
+ * Asynchronous on the stream.  Returns RBFFD_EINVAL on a bad dtype/pointer.
+ */
+rbffd_status rbffd_apply(const rbffd_op* op, const void* u, void* y, int dtype, void* stream);
+
+/* IMEX stepping parameters (Section 4.2, Section 7). */
+enum { RBFFD_MODEL_NONE = 0, RBFFD_MODEL_LINEAR = 1, RBFFD_MODEL_SCHNAKENBERG = 2,
+       RBFFD_MODEL_GRAY_SCOTT = 3, RBFFD_MODEL_BARRIO = 4 };
+typedef struct {
+    int model;          /* reaction kinetics, see coef below */
+    int nspecies;       /* 1 (u only, heat/forced diffusion) or 2 (u, v) */
+    int dtype;          /* RBFFD_F32 or RBFFD_F64 state and arithmetic
+                           (dot products always accumulate in float64) */
+    double dt;          /* time step */
+    double delta_u, delta_v;   /* diffusion coefficients */
+    double coef[8];     /* LINEAR: lu, lv.  SCHNAKENBERG: a, b, gamma.
+                           GRAY_SCOTT: F, k.  BARRIO (Eqs. turing1/2):
+                           alpha, beta, gamma, tau1, tau2 */
+    double tol;         /* BiCGSTAB relative residual tolerance */
+    int maxit;          /* BiCGSTAB iteration cap per solve */
+    int use_graph;      /* 1: replay each step from a captured CUDA graph */
+} rbffd_step_params;
+
+/*
+ * State of an IMEX run.  All vectors are caller-owned device arrays of N
+ * values of params.dtype.  u, v: current solution (updated in place);
+ * u_prev, v_prev, f_prev, g_prev: SBDF2 history (u^{n-1}, v^{n-1},
+ * f(u^{n-1}, v^{n-1}), g(...)); has_history = 0 makes the next step IMEX
+ * Euler, after which the call sets it to 1.  v, v_prev, g_prev may be NULL
+ * when nspecies = 1.
+ */
+typedef struct {
+    void* u; void* v;
+    void* u_prev; void* v_prev; void* f_prev; void* g_prev;
+    int has_history;
+    int64_t step;       /* steps taken so far (updated) */
+} rbffd_state;
+
+typedef struct {
+    int64_t steps_done;
+    int32_t max_iters_u, max_iters_v;   /* worst BiCGSTAB iteration counts */
+    int64_t total_iters;                /* sum over solves */
+    double last_relres_u, last_relres_v;
+    int64_t failed_step;                /* -1 if none */
+} rbffd_step_report;
+
+/*
+ * rbffd_step_imex - advance the semi-discrete reaction-diffusion system
+ * d/dt u = delta_u L_X u + f(u,v), d/dt v = delta_v L_X v + g(u,v)
+ * (Eq. kernel_mol; Eqs. turing1/turing2 for the paper's kinetics) by nsteps
+ * steps of SBDF2 (first step IMEX Euler without history):
+ *   (3 I - 2 dt delta L) u^{n+1} = 4 u^n - u^{n-1} + 2 dt (2 f^n - f^{n-1}),
+ * each implicit system solved by BiCGSTAB from x0 = u^n (Section 4.2).
+ * One cooperative persistent launch per step (optionally replayed from a
+ * CUDA graph).  Synchronises the stream at the end and fills report (may be
+ * NULL).  Returns RBFFD_SOLVER_NOT_CONVERGED (with report->failed_step) or
+ * RBFFD_TIMEOUT when a bounded grid barrier gave up.
+ */
+rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* state, const rbffd_step_params* params,
+                             int64_t nsteps, void* stream, rbffd_step_report* report);
+
+/*
+ * Per-stencil results of the build, in node order (device outputs, each
+ * may be NULL): eps (float64 N, in the units of the node coordinates),
+ * kappa (float64 N: kappa_2(A(eps)) at the returned eps, NaN when eps was
+ * given), evals (int32 N: kappa evaluations used), status (int32 N: the
+ * RBFFD_STENCIL_* codes).  Copies on the stream; asynchronous.
+ */
+rbffd_status rbffd_get_stencil_info(const rbffd_op* op, double* eps, double* kappa,
+                                    int32_t* evals, int32_t* status, void* stream);
+
+/*
+ * Operator rows in node order as dense padded arrays (device outputs):
+ * idx int32 N x n_max and w float64 N x n_max (entries past a row's n_k
+ * hold the row's own node and weight 0).  n_max = rbffd_op_max_n(op).
+ */
+rbffd_status rbffd_get_rows(const rbffd_op* op, int32_t* idx, double* w, void* stream);
+int64_t rbffd_op_nodes(const rbffd_op* op);
+int rbffd_op_max_n(const rbffd_op* op);
+int64_t rbffd_op_nnz(const rbffd_op* op);      /* sum of n_k (Section 4.1) */
+/* Bytes one rbffd_apply of the given dtype must move: nnz * (weight + 4)
+ * + 2 N * element size. */
+int64_t rbffd_op_apply_bytes(const rbffd_op* op, int dtype);
+void rbffd_destroy(rbffd_op* op);
+
+/* ------------------------------------------------------------------------
+ * Learned shape-parameter warm start (not in the paper; the paper's search
+ * of Section 5 stays as the fallback and the judge).
+ * Features of a stencil (3n floats): tangent-frame offsets (t1.d, t2.d,
+ * nh.d) / r_s of every stencil node (centre first), with nh oriented so
+ * sum nh.d <= 0, t1 the unit tangent part of the nearest neighbour's offset,
+ * t2 = nh x t1, r_s the largest offset.  Target: ln(eps * r_s).
+ * Network: 3n -> 64 -> 64 -> 1, GELU (erf form) hidden layers, float32.
+ * Flat parameter layout: W1 (row-major 3n x 64), b1[64], W2 (64 x 64),
+ * b2[64], W3[64], b3[1].
+ * ---------------------------------------------------------------------- */
+
+/* Number of float parameters for stencil size n. */
+int64_t rbffd_mlp_param_count(int n);
+/* Create a network for stencil size n from host float32 params (layout
+ * above; NULL = zeros). */
+rbffd_status rbffd_mlp_create(int n, const float* params_host, rbffd_mlp** out);
+rbffd_status rbffd_mlp_get_params(const rbffd_mlp* mlp, float* params_host);
+void rbffd_mlp_destroy(rbffd_mlp* mlp);
+
+/*
+ * Features of the stencils of every node whose stencil size is n, in node
+ * order (device out: count x 3n float32, count = number of such nodes,
+ * returned in *count_host) and, when target is not NULL, the training target
+ * ln(eps * r_s) from the operator's eps (device out: count float32).
+ * nodes / normals must be the arrays the operator was built from.
+ */
+rbffd_status rbffd_features(const rbffd_op* op, const double* nodes, const double* normals,
+                            int n, float* feats, float* target, int64_t* count_host,
+                            void* stream);
+
+/*
+ * One forward + backward pass of the MSE loss over a batch (device inputs
+ * feats count x 3n, target count; device outputs grad (param_count floats)
+ * and loss (1 float)).  Used to check gradients against the oracle.
+ */
+rbffd_status rbffd_mlp_loss_grad(const rbffd_mlp* mlp, const float* feats, const float* target,
+                                 int64_t count, float* grad, float* loss, void* stream);
+
+/*
+ * Adam training on the device: epochs passes over (feats, target) in
+ * seeded shuffled mini-batches of `batch`; lr, beta1 0.9, beta2 0.999,
+ * eps 1e-8.  loss_host (may be NULL) receives the mean loss of each epoch.
+ * Synchronises the stream.
+ */
+rbffd_status rbffd_mlp_train(rbffd_mlp* mlp, const float* feats, const float* target,
+                             int64_t count, int epochs, int batch, float lr, uint64_t seed,
+                             void* stream, float* loss_host);
+
+/* Predictions ln(eps * r_s) for count feature rows (device in / out). */
+rbffd_status rbffd_mlp_predict(const rbffd_mlp* mlp, const float* feats, int64_t count,
+                               float* out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+const char* rbffd_status_str(rbffd_status s);
+const char* rbffd_last_error(void);
+/* Device FP64 FMA throughput microbenchmark (GFLOP/s, 2 flops per FMA),
+ * used to report the build's roofline.  Synchronises the stream. */
+rbffd_status rbffd_fp64_peak(void* stream, double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBFFD_H */

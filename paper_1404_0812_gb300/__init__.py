@@ -1,0 +1,222 @@
+"""GB300-native RBF-FD discrete Laplace-Beltrami operator (sm_103a).
+
+Python binding of the C ABI in ``include/rbffd.h``, with the same names:
+``build_operator``, ``apply``, ``step_imex``, ``get_stencil_info``,
+``get_rows``, ``destroy`` and the learned-eps calls.  The functions only
+marshal arguments (torch tensors provide device memory and streams); all
+arithmetic runs in the CUDA library, and a missing library is an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib
+from ._lib import (F32, F64, GAUSSIAN, IMQ, MODEL_BARRIO, MODEL_GRAY_SCOTT, MODEL_LINEAR,
+                   MODEL_NONE, MODEL_SCHNAKENBERG, RbffdError)
+
+KERNELS = {"gaussian": GAUSSIAN, "imq": IMQ}
+MODELS = {"none": MODEL_NONE, "linear": MODEL_LINEAR, "schnakenberg": MODEL_SCHNAKENBERG,
+          "gray_scott": MODEL_GRAY_SCOTT, "barrio": MODEL_BARRIO}
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+class Operator:
+    """Handle of a library-owned operator (rbffd_op)."""
+
+    def __init__(self, handle, N, kernel):
+        self.handle = handle
+        self.N = N
+        self.kernel = kernel
+
+    @property
+    def nnz(self) -> int:
+        return int(_lib.load().rbffd_op_nnz(self.handle))
+
+    @property
+    def n_max(self) -> int:
+        return int(_lib.load().rbffd_op_max_n(self.handle))
+
+    def apply_bytes(self, dtype=F32) -> int:
+        return int(_lib.load().rbffd_op_apply_bytes(self.handle, dtype))
+
+    def __del__(self):
+        try:
+            destroy(self)
+        except Exception:
+            pass
+
+
+def build_operator(nodes, normals, n=31, kernel="imq", kappa_target=1e12, eps_tol=1e-4,
+                   max_evals=64, eps_override=None, mlps=None, accept=(0.5, 2.0),
+                   block_threads=0, blocks_per_sm=0, stream=None, allow_failures=False):
+    """rbffd_build_operator.  ``n`` is an int or a CUDA int32 tensor (N,);
+    ``mlps`` a list of EpsNet to warm-start the search."""
+    lib = _lib.load()
+    nodes = _dev(nodes, torch.float64)
+    normals = _dev(normals, torch.float64)
+    N = nodes.shape[0]
+    o = _lib.BuildOpts()
+    lib.rbffd_build_opts_default(C.byref(o))
+    o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    o.kappa_target = float(kappa_target)
+    o.eps_tol = float(eps_tol)
+    o.max_evals = int(max_evals)
+    o.accept_lo, o.accept_hi = float(accept[0]), float(accept[1])
+    if eps_override is not None:
+        eps_override = _dev(eps_override, torch.float64)
+        o.eps_override = eps_override.data_ptr()
+    if mlps:
+        o.use_learned = 1
+        for i, m in enumerate(mlps):
+            o.mlp[i] = m.handle
+    o.block_threads, o.blocks_per_sm = int(block_threads), int(blocks_per_sm)
+    if isinstance(n, torch.Tensor):
+        npn = _dev(n, torch.int32)
+        nptr, nu = C.c_void_p(npn.data_ptr()), 0
+    else:
+        nptr, nu = None, int(n)
+    h = C.c_void_p()
+    st = lib.rbffd_build_operator(C.c_void_p(nodes.data_ptr()), C.c_void_p(normals.data_ptr()), N,
+                                  nptr, nu, C.byref(o), _stream(stream), C.byref(h))
+    allow = (_lib.EPS_SEARCH_FAILED, _lib.ESINGULAR) if allow_failures else ()
+    _lib.check(st, "rbffd_build_operator", allow)
+    op = Operator(h, N, o.kernel)
+    op.status = st
+    return op
+
+
+def apply(op: Operator, u, y=None, stream=None):
+    """rbffd_apply: y = L_X u (float32 or float64 by u's dtype)."""
+    lib = _lib.load()
+    dt = F32 if u.dtype == torch.float32 else F64
+    u = _dev(u, u.dtype)
+    if y is None:
+        y = torch.empty_like(u)
+    _lib.check(lib.rbffd_apply(op.handle, _ptr(u), _ptr(y), dt, _stream(stream)), "rbffd_apply")
+    return y
+
+
+def get_stencil_info(op: Operator, stream=None):
+    """rbffd_get_stencil_info -> dict(eps, kappa, evals, status) CUDA tensors."""
+    lib = _lib.load()
+    dev = torch.device("cuda")
+    out = dict(eps=torch.empty(op.N, dtype=torch.float64, device=dev),
+               kappa=torch.empty(op.N, dtype=torch.float64, device=dev),
+               evals=torch.empty(op.N, dtype=torch.int32, device=dev),
+               status=torch.empty(op.N, dtype=torch.int32, device=dev))
+    _lib.check(lib.rbffd_get_stencil_info(op.handle, _ptr(out["eps"]), _ptr(out["kappa"]),
+                                          _ptr(out["evals"]), _ptr(out["status"]), _stream(stream)),
+               "rbffd_get_stencil_info")
+    return out
+
+
+def get_rows(op: Operator, stream=None):
+    """rbffd_get_rows -> (idx int32 N x n_max, w float64 N x n_max)."""
+    lib = _lib.load()
+    nm = op.n_max
+    idx = torch.empty((op.N, nm), dtype=torch.int32, device="cuda")
+    w = torch.empty((op.N, nm), dtype=torch.float64, device="cuda")
+    _lib.check(lib.rbffd_get_rows(op.handle, _ptr(idx), _ptr(w), _stream(stream)), "rbffd_get_rows")
+    return idx, w
+
+
+def destroy(op: Operator):
+    if op is not None and op.handle:
+        _lib.load().rbffd_destroy(op.handle)
+        op.handle = None
+
+
+@dataclass
+class StepParams:
+    model: str = "none"
+    nspecies: int = 1
+    dtype: torch.dtype = torch.float64
+    dt: float = 1e-4
+    delta_u: float = 1.0
+    delta_v: float = 0.0
+    coef: tuple = ()
+    tol: float = 1e-12
+    maxit: int = 200
+    use_graph: bool = False
+
+
+@dataclass
+class StepState:
+    """Caller-owned CUDA vectors of one IMEX run (see rbffd_state)."""
+    u: torch.Tensor
+    v: torch.Tensor | None = None
+    u_prev: torch.Tensor | None = None
+    v_prev: torch.Tensor | None = None
+    f_prev: torch.Tensor | None = None
+    g_prev: torch.Tensor | None = None
+    has_history: int = 0
+    step: int = 0
+
+    @staticmethod
+    def create(u, v=None):
+        z = lambda t: None if t is None else torch.zeros_like(t)
+        return StepState(u=u, v=v, u_prev=z(u), v_prev=z(v), f_prev=z(u), g_prev=z(v))
+
+
+def model_coefs(p: dict):
+    """(model name, coef tuple) from a reaction parameter dict."""
+    m = p["model"]
+    if m == "linear":
+        return m, (p["lu"], p["lv"])
+    if m == "schnakenberg":
+        return m, (p["a"], p["b"], p["gamma"])
+    if m == "gray_scott":
+        return m, (p["F"], p["k"])
+    if m == "barrio":
+        return m, (p["alpha"], p["beta"], p["gamma"], p["tau1"], p["tau2"])
+    return "none", ()
+
+
+def step_imex(op: Operator, state: StepState, params: StepParams, nsteps: int, stream=None,
+              allow_failure=False):
+    """rbffd_step_imex; updates ``state`` in place and returns the report."""
+    lib = _lib.load()
+    sp = _lib.StepParams()
+    sp.model = MODELS[params.model]
+    sp.nspecies = params.nspecies
+    sp.dtype = F32 if params.dtype == torch.float32 else F64
+    sp.dt, sp.delta_u, sp.delta_v = params.dt, params.delta_u, params.delta_v
+    for i, c in enumerate(params.coef):
+        sp.coef[i] = c
+    sp.tol, sp.maxit, sp.use_graph = params.tol, params.maxit, int(params.use_graph)
+    cs = _lib.State(_ptr(state.u), _ptr(state.v), _ptr(state.u_prev), _ptr(state.v_prev),
+                    _ptr(state.f_prev), _ptr(state.g_prev), state.has_history, state.step)
+    rep = _lib.StepReport()
+    st = lib.rbffd_step_imex(op.handle, C.byref(cs), C.byref(sp), int(nsteps), _stream(stream),
+                             C.byref(rep))
+    state.has_history, state.step = cs.has_history, cs.step
+    allow = (_lib.SOLVER_NOT_CONVERGED,) if allow_failure else ()
+    _lib.check(st, "rbffd_step_imex", allow)
+    return dict(status=st, steps_done=rep.steps_done, max_iters_u=rep.max_iters_u,
+                max_iters_v=rep.max_iters_v, total_iters=rep.total_iters,
+                last_relres_u=rep.last_relres_u, last_relres_v=rep.last_relres_v,
+                failed_step=rep.failed_step)
+
+
+def fp64_peak(stream=None) -> float:
+    """FP64 FMA throughput of this GPU in GFLOP/s (microbenchmark)."""
+    g = C.c_double()
+    _lib.check(_lib.load().rbffd_fp64_peak(_stream(stream), C.byref(g)), "rbffd_fp64_peak")
+    return g.value

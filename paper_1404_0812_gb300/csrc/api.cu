@@ -1,0 +1,307 @@
+// C ABI entry points (include/rbffd.h): argument checks, operator storage,
+// and the order of the build phases.  The arithmetic lives in knn.cu,
+// build.cu, apply.cu, step.cu and mlp.cu.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <map>
+#include <vector>
+
+namespace rbffd {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+rbffd_status apply_launch(const rbffd_op* op, const void* u, void* y, int dtype, cudaStream_t st);
+
+namespace {
+
+__global__ void iota_kernel(int32_t* a, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (int32_t)i;
+}
+
+__global__ void init_info(double* eps, double* kappa, int32_t* evals, int32_t* status,
+                          const double* eps_override, int64_t N) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    eps[i] = eps_override ? eps_override[i] : NAN;
+    kappa[i] = NAN;
+    evals[i] = 0;
+    status[i] = RBFFD_STENCIL_OK;
+}
+
+__global__ void count_status(const int32_t* status, int64_t N, int* bad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int s = status[i];
+    if (s != RBFFD_STENCIL_OK && s != RBFFD_STENCIL_ACCEPTED_PREDICTION) atomicAdd(bad, 1);
+}
+
+__global__ void rows_kernel(const int32_t* __restrict__ idx, const double* __restrict__ w,
+                            const int32_t* __restrict__ row_node, GroupInfo gi, int nmax, int64_t R,
+                            int32_t* __restrict__ out_idx, double* __restrict__ out_w) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int g = group_of_row(gi, r);
+    int n = gi.n[g], npad = gi.npad[g];
+    int64_t lr = r - gi.row_begin[g];
+    int node = row_node[r];
+    for (int j = 0; j < nmax; ++j) {
+        int32_t id = node;
+        double wv = 0.0;
+        if (j < n) {
+            int64_t e = ell_elem(gi.ell_off[g], npad, lr, j);
+            id = idx[e];
+            wv = w[e];
+        }
+        if (out_idx) out_idx[(int64_t)node * nmax + j] = id;
+        if (out_w) out_w[(int64_t)node * nmax + j] = wv;
+    }
+}
+
+void free_op(rbffd_op* op) {
+    if (!op) return;
+    cudaFree(op->row_node);
+    cudaFree(op->idx);
+    cudaFree(op->w64);
+    cudaFree(op->w32);
+    cudaFree(op->eps);
+    cudaFree(op->kappa);
+    cudaFree(op->evals);
+    cudaFree(op->status);
+    if (op->step) step_ws_free(op->step);
+    delete op;
+}
+
+}  // namespace
+}  // namespace rbffd
+
+using namespace rbffd;
+
+extern "C" {
+
+const char* rbffd_last_error(void) { return g_err; }
+
+const char* rbffd_status_str(rbffd_status s) {
+    switch (s) {
+        case RBFFD_OK: return "ok";
+        case RBFFD_EINVAL: return "invalid argument";
+        case RBFFD_ECUDA: return "CUDA error";
+        case RBFFD_ENOMEM: return "out of device memory";
+        case RBFFD_EPS_SEARCH_FAILED: return "shape-parameter search failed for some stencils";
+        case RBFFD_SOLVER_NOT_CONVERGED: return "BiCGSTAB did not converge";
+        case RBFFD_TIMEOUT: return "device-side wait timed out";
+        case RBFFD_NOT_IMPLEMENTED: return "not implemented";
+        case RBFFD_ESINGULAR: return "local interpolation matrix not positive definite";
+    }
+    return "unknown status";
+}
+
+void rbffd_build_opts_default(rbffd_build_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->kernel = RBFFD_IMQ;
+    o->kappa_target = 1e12;
+    o->eps_tol = 1e-4;
+    o->max_evals = 64;
+    o->use_learned = 0;
+    o->accept_lo = 0.5;
+    o->accept_hi = 2.0;
+}
+
+rbffd_status rbffd_build_operator(const double* nodes, const double* normals, int64_t N,
+                                  const int32_t* n_per_node, int n_uniform,
+                                  const rbffd_build_opts* opts_in, void* stream, rbffd_op** out) {
+    RBFFD_CHECK_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    RBFFD_CHECK_ARG(nodes != nullptr && normals != nullptr, "nodes / normals are NULL");
+    RBFFD_CHECK_ARG(N >= 2 && N < (int64_t)1 << 31, "N must be in [2, 2^31)");
+    rbffd_build_opts o;
+    if (opts_in) o = *opts_in; else rbffd_build_opts_default(&o);
+    RBFFD_CHECK_ARG(o.kernel == RBFFD_GAUSSIAN || o.kernel == RBFFD_IMQ, "kernel");
+    RBFFD_CHECK_ARG(o.eps_override || (o.kappa_target > 1.0 && std::isfinite(o.kappa_target)),
+                    "kappa_target must be > 1");
+    RBFFD_CHECK_ARG(o.eps_override || o.eps_tol > 0.0, "eps_tol must be > 0");
+    RBFFD_CHECK_ARG(o.eps_override || o.max_evals >= 2, "max_evals must be >= 2");
+    RBFFD_CHECK_ARG(!o.use_learned || (o.accept_lo > 0 && o.accept_hi >= o.accept_lo), "accept band");
+    cudaStream_t st = as_stream(stream);
+
+    // ---- stencil-size groups (sorted by descending n; stable node order)
+    std::vector<int32_t> hn;
+    std::map<int, int64_t> counts;
+    if (n_per_node) {
+        hn.resize(N);
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(hn.data(), n_per_node, N * sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < N; ++i) counts[hn[i]]++;
+    } else {
+        counts[n_uniform] = N;
+    }
+    RBFFD_CHECK_ARG((int)counts.size() <= RBFFD_MAX_GROUPS, "more than 8 distinct stencil sizes");
+    for (auto& kv : counts) {
+        RBFFD_CHECK_ARG(kv.first >= 2 && kv.first <= RBFFD_MAX_N, "stencil size must be in [2, 128]");
+        RBFFD_CHECK_ARG(kv.first <= N, "stencil size exceeds the number of nodes");
+    }
+    rbffd_op* op = new rbffd_op();
+    memset(op, 0, sizeof(*op));
+    op->N = N;
+    op->kernel = o.kernel;
+    op->kappa_target = o.kappa_target;
+    GroupInfo& gi = op->gi;
+    gi.ngroups = (int)counts.size();
+    {
+        int g = 0;
+        int64_t row = 0, elem = 0;
+        for (auto it = counts.rbegin(); it != counts.rend(); ++it, ++g) {
+            gi.n[g] = it->first;
+            gi.npad[g] = (it->first + 3) / 4 * 4;
+            gi.row_begin[g] = row;
+            gi.ell_off[g] = elem;
+            row += it->second;
+            elem += (it->second + ELL_SLICE - 1) / ELL_SLICE * ELL_SLICE * gi.npad[g];
+            op->nnz += it->second * it->first;
+            op->n_max = std::max(op->n_max, it->first);
+        }
+        gi.row_begin[g] = row;
+        gi.ell_off[g] = elem;
+        op->ell_elems = elem;
+    }
+    auto fail = [&](rbffd_status s) {
+        free_op(op);
+        return s;
+    };
+#define TRY_OP(expr)                                                                   \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess) {                                                       \
+            set_error("%s: %s", #expr, cudaGetErrorString(_e));                       \
+            return fail(_e == cudaErrorMemoryAllocation ? RBFFD_ENOMEM : RBFFD_ECUDA); \
+        }                                                                              \
+    } while (0)
+    TRY_OP(cudaMalloc(&op->row_node, N * sizeof(int32_t)));
+    TRY_OP(cudaMalloc(&op->idx, op->ell_elems * sizeof(int32_t)));
+    TRY_OP(cudaMalloc(&op->w64, op->ell_elems * sizeof(double)));
+    TRY_OP(cudaMalloc(&op->w32, op->ell_elems * sizeof(float)));
+    TRY_OP(cudaMalloc(&op->eps, N * sizeof(double)));
+    TRY_OP(cudaMalloc(&op->kappa, N * sizeof(double)));
+    TRY_OP(cudaMalloc(&op->evals, N * sizeof(int32_t)));
+    TRY_OP(cudaMalloc(&op->status, N * sizeof(int32_t)));
+    TRY_OP(cudaMemsetAsync(op->idx, 0, op->ell_elems * sizeof(int32_t), st));
+    TRY_OP(cudaMemsetAsync(op->w64, 0, op->ell_elems * sizeof(double), st));
+    TRY_OP(cudaMemsetAsync(op->w32, 0, op->ell_elems * sizeof(float), st));
+    if (n_per_node) {
+        std::vector<int32_t> rn(N);
+        std::vector<int64_t> pos(gi.ngroups);
+        for (int g = 0; g < gi.ngroups; ++g) pos[g] = gi.row_begin[g];
+        for (int64_t i = 0; i < N; ++i) {
+            int g = 0;
+            while (gi.n[g] != hn[i]) ++g;
+            rn[pos[g]++] = (int32_t)i;
+        }
+        TRY_OP(cudaMemcpyAsync(op->row_node, rn.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY_OP(cudaStreamSynchronize(st));
+    } else {
+        iota_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->row_node, N);
+        TRY_OP(cudaGetLastError());
+    }
+    init_info<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->eps, op->kappa, op->evals, op->status,
+                                                           o.eps_override, N);
+    TRY_OP(cudaGetLastError());
+
+    // ---- stencils
+    rbffd_status s = knn_stencils(op, nodes, normals, st);
+    if (s != RBFFD_OK) return fail(s);
+
+    // ---- shape parameters
+    rbffd_status search_status = RBFFD_OK;
+    if (!o.eps_override) {
+        float* guess = nullptr;
+        if (o.use_learned) {
+            TRY_OP(cudaMallocAsync(&guess, N * sizeof(float), st));
+            s = mlp_guess(op, nodes, normals, o, guess, st);
+            if (s != RBFFD_OK) {
+                cudaFreeAsync(guess, st);
+                return fail(s);
+            }
+        }
+        s = build_search(op, nodes, normals, o, guess, st);
+        if (guess) cudaFreeAsync(guess, st);
+        if (s != RBFFD_OK) return fail(s);
+        int* bad = nullptr;
+        TRY_OP(cudaMallocAsync(&bad, sizeof(int), st));
+        TRY_OP(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        count_status<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->status, N, bad);
+        int hb = 0;
+        TRY_OP(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY_OP(cudaStreamSynchronize(st));
+        cudaFreeAsync(bad, st);
+        if (hb) {
+            set_error("eps search failed for %d stencils", hb);
+            search_status = RBFFD_EPS_SEARCH_FAILED;
+        }
+    }
+    // ---- weights
+    s = build_weights(op, nodes, normals, o, op->eps, st);
+    if (s != RBFFD_OK && s != RBFFD_ESINGULAR) return fail(s);
+    TRY_OP(cudaStreamSynchronize(st));
+    *out = op;
+    if (search_status != RBFFD_OK) return search_status;
+    return s;
+#undef TRY_OP
+}
+
+rbffd_status rbffd_apply(const rbffd_op* op, const void* u, void* y, int dtype, void* stream) {
+    RBFFD_CHECK_ARG(op && u && y, "NULL argument");
+    RBFFD_CHECK_ARG(dtype == RBFFD_F32 || dtype == RBFFD_F64, "dtype");
+    RBFFD_CHECK_ARG(u != y, "u and y alias");
+    return apply_launch(op, u, y, dtype, as_stream(stream));
+}
+
+rbffd_status rbffd_get_stencil_info(const rbffd_op* op, double* eps, double* kappa, int32_t* evals,
+                                    int32_t* status, void* stream) {
+    RBFFD_CHECK_ARG(op, "op is NULL");
+    cudaStream_t st = as_stream(stream);
+    if (eps) RBFFD_CUDA_TRY(cudaMemcpyAsync(eps, op->eps, op->N * 8, cudaMemcpyDeviceToDevice, st));
+    if (kappa) RBFFD_CUDA_TRY(cudaMemcpyAsync(kappa, op->kappa, op->N * 8, cudaMemcpyDeviceToDevice, st));
+    if (evals) RBFFD_CUDA_TRY(cudaMemcpyAsync(evals, op->evals, op->N * 4, cudaMemcpyDeviceToDevice, st));
+    if (status) RBFFD_CUDA_TRY(cudaMemcpyAsync(status, op->status, op->N * 4, cudaMemcpyDeviceToDevice, st));
+    return RBFFD_OK;
+}
+
+rbffd_status rbffd_get_rows(const rbffd_op* op, int32_t* idx, double* w, void* stream) {
+    RBFFD_CHECK_ARG(op, "op is NULL");
+    cudaStream_t st = as_stream(stream);
+    rows_kernel<<<(unsigned)((op->N + 127) / 128), 128, 0, st>>>(op->idx, op->w64, op->row_node, op->gi,
+                                                                 op->n_max, op->N, idx, w);
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    return RBFFD_OK;
+}
+
+int64_t rbffd_op_nodes(const rbffd_op* op) { return op ? op->N : 0; }
+int rbffd_op_max_n(const rbffd_op* op) { return op ? op->n_max : 0; }
+int64_t rbffd_op_nnz(const rbffd_op* op) { return op ? op->nnz : 0; }
+int64_t rbffd_op_apply_bytes(const rbffd_op* op, int dtype) {
+    if (!op) return 0;
+    int64_t ws = dtype == RBFFD_F32 ? 4 : 8;
+    return op->nnz * (ws + 4) + 2 * op->N * ws;
+}
+void rbffd_destroy(rbffd_op* op) { free_op(op); }
+
+}  // extern "C"

@@ -1,0 +1,878 @@
+// Batched per-stencil build of the RBF-FD surface Laplacian (Sections 2-5).
+//
+// GB300 design.  The local algebra must be float64 (kappa_T ~ 1e12 leaves
+// about four digits), and GB300's FP64 rate is a few operations per clock
+// per SM, so every FP64 warp instruction has to do 32 useful operations.
+// One thread owns one stencil ("lane per stencil"): all lanes of a warp run
+// the same instruction stream on different stencils, with no shuffles and no
+// idle lanes inside the O(m^3) factorisations.  Each lane's matrices live
+// in a global scratch area interleaved across the 32 lanes of its warp, so
+// every load is one 256-byte coalesced transaction (L1/L2 cached).
+// The factorisation is a packed lower Cholesky of Phi with 4x4 register
+// tiles (16 FMAs per 8 loads).
+//
+// Condition number (Section 5, kappa_2 of the symmetric augmented A of
+// Eq. rbf_linsys): Phi is positive definite for the Gaussian and IMQ
+// kernels, so A = [[Phi, 1], [1^T, 0]] is solved through Phi = L L^T and
+// its Schur complement s = 1^T Phi^{-1} 1.  max|lambda(A)| comes from a
+// short Lanczos run with A (A x formed as L (L^T x) plus the border), and
+// 1 / min|lambda(A)| from a short Lanczos run with A^{-1}; each run stops
+// when its extreme Ritz value settles (relative change 1e-6).  The Ritz
+// values of the small tridiagonal are found by Sturm-count bisection in
+// float32 (relative accuracy ~1e-7, far below the float64 noise of kappa).
+//
+// Shape parameter search (Eq. target_cond): F(x) = ln(kappa(A(e^x)) /
+// kappa_T) in x = ln(eps * r_s) (coordinates translated to the stencil
+// centre and scaled by the stencil radius r_s).  Bracket by secant steps
+// from the oracle's starting point (eps_0 = 1 / mean neighbour distance) or
+// from a learned prediction, then Brent-Dekker in x to the absolute eps
+// tolerance.  Lanes that finish take the next stencil from a global counter,
+// so a warp stays full until the work runs out.  Groups of different stencil
+// size are processed largest first in the same persistent launch.
+//
+// Weights (Eqs. grad_x_f_interp, surface_lap_P1): only the first row of
+// L_P = sum_d G^d G^d is needed, so with A symmetric
+//   g_d = (A^{-1} [B^d row 0; 0])[:n],  v = sum_d B^{dT} g_d,
+//   w = (A^{-1} [v; 0])[:n] / r_s^2,
+// four solves and one pass over the pairs, equal in exact arithmetic to
+// forming the full G^d (which the oracle does).
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace rbffd {
+namespace {
+
+constexpr int LANCZOS_KMAX = 24;
+constexpr double LANCZOS_RTOL = 1e-6;
+constexpr double F_FAIL = 60.0;         // F value used when Phi is not numerically SPD
+constexpr int BRACKET_MAX = 40;
+
+// ---------------------------------------------------------------------------
+// lane-private scratch, interleaved across the warp
+// ---------------------------------------------------------------------------
+struct Lane {
+    double* p;   // points at element 0 of this lane
+    __device__ __forceinline__ double& operator[](int e) const { return p[(int64_t)e * 32]; }
+};
+
+__host__ __device__ inline int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+struct Layout {
+    int m;       // padded stencil size (multiple of 4)
+    int P;       // m (m + 1) / 2
+    int R2, L, PH, XS, NS, U, ID, Q0, Q1, Q2, T0, GV, HV;
+    int size;    // doubles per lane
+};
+
+__host__ __device__ inline Layout make_layout(int m) {
+    Layout l;
+    l.m = m;
+    l.P = m * (m + 1) / 2;
+    int o = 0;
+    l.R2 = o; o += l.P;
+    l.L = o; o += l.P;
+    l.PH = o; o += l.P;
+    l.XS = o; o += 3 * m;
+    l.NS = o; o += 3 * m;
+    l.U = o; o += m;
+    l.ID = o; o += m;
+    l.Q0 = o; o += m;
+    l.Q1 = o; o += m;
+    l.Q2 = o; o += m;
+    l.T0 = o; o += m;
+    l.GV = o; o += 3 * m;
+    l.HV = o; o += 3 * m;
+    l.size = o;
+    return l;
+}
+
+// ---------------------------------------------------------------------------
+// kernels phi(eps r) and psi(r) = phi'(r)/r as functions of e2r2 = (eps r)^2
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double phi_of(int kernel, double e2r2) {
+    return kernel == RBFFD_GAUSSIAN ? exp(-e2r2) : rsqrt(1.0 + e2r2);
+}
+// psi in scaled units: Gaussian -2 eps^2 phi, IMQ -eps^2 phi^3
+__device__ __forceinline__ double psi_from_phi(int kernel, double e2, double ph) {
+    return kernel == RBFFD_GAUSSIAN ? -2.0 * e2 * ph : -e2 * ph * ph * ph;
+}
+
+// ---------------------------------------------------------------------------
+// stencil geometry: centre-translated, r_s-scaled coordinates and normals
+// ---------------------------------------------------------------------------
+struct Geo {
+    double rs;        // stencil radius (max distance to the centre)
+    double mean_d;    // mean scaled distance of the n-1 neighbours
+};
+
+__device__ Geo load_geometry(const Lane& S, const Layout& ly, int n, const int32_t* __restrict__ idx,
+                             int64_t off, int npad, int64_t lr, const double* __restrict__ X,
+                             const double* __restrict__ NR, bool with_normals) {
+    int c = idx[ell_elem(off, npad, lr, 0)];
+    double cx = X[3 * (int64_t)c], cy = X[3 * (int64_t)c + 1], cz = X[3 * (int64_t)c + 2];
+    double rs2 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        int k = idx[ell_elem(off, npad, lr, j)];
+        double dx = X[3 * (int64_t)k] - cx, dy = X[3 * (int64_t)k + 1] - cy,
+               dz = X[3 * (int64_t)k + 2] - cz;
+        S[ly.XS + j] = dx;
+        S[ly.XS + ly.m + j] = dy;
+        S[ly.XS + 2 * ly.m + j] = dz;
+        rs2 = fmax(rs2, dx * dx + dy * dy + dz * dz);
+        if (with_normals) {
+            double nx = NR[3 * (int64_t)k], ny = NR[3 * (int64_t)k + 1], nz = NR[3 * (int64_t)k + 2];
+            double inv = rsqrt(nx * nx + ny * ny + nz * nz);
+            S[ly.NS + j] = nx * inv;
+            S[ly.NS + ly.m + j] = ny * inv;
+            S[ly.NS + 2 * ly.m + j] = nz * inv;
+        }
+    }
+    Geo g;
+    g.rs = sqrt(rs2);
+    double inv = 1.0 / g.rs;
+    double sum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double x = S[ly.XS + j] * inv, y = S[ly.XS + ly.m + j] * inv, z = S[ly.XS + 2 * ly.m + j] * inv;
+        S[ly.XS + j] = x;
+        S[ly.XS + ly.m + j] = y;
+        S[ly.XS + 2 * ly.m + j] = z;
+        if (j > 0) sum += sqrt(x * x + y * y + z * z);
+    }
+    g.mean_d = sum / (double)(n - 1);
+    // pairwise squared distances (lower triangle, diagonal 0)
+    for (int i = 0; i < n; ++i) {
+        double xi = S[ly.XS + i], yi = S[ly.XS + ly.m + i], zi = S[ly.XS + 2 * ly.m + i];
+        int base = pk(i, 0);
+        for (int j = 0; j < i; ++j) {
+            double dx = xi - S[ly.XS + j], dy = yi - S[ly.XS + ly.m + j], dz = zi - S[ly.XS + 2 * ly.m + j];
+            S[ly.R2 + base + j] = dx * dx + dy * dy + dz * dz;
+        }
+        S[ly.R2 + base + i] = 0.0;
+    }
+    return g;
+}
+
+// Phi(eps) into region dst (lower packed, m x m, identity on the padding);
+// optionally a copy into region cpy.
+__device__ void assemble_phi(const Lane& S, const Layout& ly, int n, int kernel, double eps_s,
+                             int dst, int cpy) {
+    double e2 = eps_s * eps_s;
+    for (int i = 0; i < ly.m; ++i) {
+        int base = pk(i, 0);
+        if (i < n) {
+            for (int j = 0; j < i; ++j) {
+                double v = phi_of(kernel, e2 * S[ly.R2 + base + j]);
+                S[dst + base + j] = v;
+                if (cpy >= 0) S[cpy + base + j] = v;
+            }
+        } else {
+            for (int j = 0; j < i; ++j) {
+                S[dst + base + j] = 0.0;
+                if (cpy >= 0) S[cpy + base + j] = 0.0;
+            }
+        }
+        S[dst + base + i] = 1.0;
+        if (cpy >= 0) S[cpy + base + i] = 1.0;
+    }
+}
+
+// In-place packed Cholesky Phi = L L^T (left-looking, 4x4 register tiles).
+// ID receives 1 / L_ii.  Returns false when a pivot is not positive.
+__device__ bool cholesky(const Lane& S, const Layout& ly) {
+    const int m = ly.m, L = ly.L;
+    bool ok = true;
+    for (int jb = 0; jb < m; jb += 4) {
+        double Ld[4][4];
+        for (int ib = jb; ib < m; ib += 4) {
+            double acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    acc[a][b] = (ib + a >= jb + b) ? S[L + pk(ib + a, jb + b)] : 0.0;
+            for (int k = 0; k < jb; ++k) {
+                double xa[4], yb[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xa[a] = S[L + pk(ib + a, k)];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) yb[b] = S[L + pk(jb + b, k)];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(-xa[a], yb[b], acc[a][b]);
+            }
+            if (ib == jb) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    double d = acc[b][b];
+                    if (!(d > 0.0)) {
+                        ok = false;
+                        d = 1.0;
+                    }
+                    double l = sqrt(d);
+                    double il = 1.0 / l;
+                    acc[b][b] = l;
+                    S[ly.ID + jb + b] = il;
+#pragma unroll
+                    for (int a = b + 1; a < 4; ++a) acc[a][b] *= il;
+#pragma unroll
+                    for (int c = b + 1; c < 4; ++c)
+#pragma unroll
+                        for (int a = c; a < 4; ++a) acc[a][c] = fma(-acc[a][b], acc[c][b], acc[a][c]);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b <= a; ++b) {
+                        Ld[a][b] = acc[a][b];
+                        S[L + pk(jb + a, jb + b)] = acc[a][b];
+                    }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        double v = acc[a][b];
+#pragma unroll
+                        for (int c = 0; c < b; ++c) v = fma(-acc[a][c], Ld[b][c], v);
+                        acc[a][b] = v * S[ly.ID + jb + b];
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) S[L + pk(ib + a, jb + b)] = acc[a][b];
+                }
+            }
+        }
+        if (!ok) return false;
+    }
+    return true;
+}
+
+// x <- Phi^{-1} x (x in region V of length m) using L and ID.
+__device__ void chol_solve(const Lane& S, const Layout& ly, int V) {
+    const int m = ly.m, L = ly.L;
+    // forward: L y = x
+    for (int ib = 0; ib < m; ib += 4) {
+        double t[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = S[V + ib + a];
+        for (int k = 0; k < ib; ++k) {
+            double yk = S[V + k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) t[a] = fma(-S[L + pk(ib + a, k)], yk, t[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int c = 0; c < a; ++c) t[a] = fma(-S[L + pk(ib + a, ib + c)], t[c], t[a]);
+            t[a] *= S[ly.ID + ib + a];
+            S[V + ib + a] = t[a];
+        }
+    }
+    // backward: L^T x = y
+    for (int kb = m - 4; kb >= 0; kb -= 4) {
+        double t[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) t[b] = S[V + kb + b];
+#pragma unroll
+        for (int b = 3; b >= 0; --b) {
+#pragma unroll
+            for (int c = b + 1; c < 4; ++c) t[b] = fma(-S[L + pk(kb + c, kb + b)], t[c], t[b]);
+            t[b] *= S[ly.ID + kb + b];
+            S[V + kb + b] = t[b];
+        }
+        const int r0 = pk(kb, 0), r1 = pk(kb + 1, 0), r2 = pk(kb + 2, 0), r3 = pk(kb + 3, 0);
+        for (int i = 0; i < kb; ++i) {
+            double v = S[V + i];
+            v = fma(-S[L + r0 + i], t[0], v);
+            v = fma(-S[L + r1 + i], t[1], v);
+            v = fma(-S[L + r2 + i], t[2], v);
+            v = fma(-S[L + r3 + i], t[3], v);
+            S[V + i] = v;
+        }
+    }
+}
+
+// y <- Phi x = L (L^T x); x in region VX, y in region VY (distinct), uses T0.
+__device__ void chol_mul(const Lane& S, const Layout& ly, int VX, int VY) {
+    const int m = ly.m, L = ly.L, T = ly.T0;
+    for (int i = 0; i < m; ++i) S[T + i] = 0.0;
+    // t = L^T x : t_i += L(k, i) x_k
+    for (int k = 0; k < m; ++k) {
+        double xk = S[VX + k];
+        int r = pk(k, 0);
+        for (int i = 0; i <= k; ++i) S[T + i] = fma(S[L + r + i], xk, S[T + i]);
+    }
+    // y = L t
+    for (int i = 0; i < m; ++i) {
+        int r = pk(i, 0);
+        double acc = 0.0;
+        for (int k = 0; k <= i; ++k) acc = fma(S[L + r + k], S[T + k], acc);
+        S[VY + i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// extreme eigenvalues of a symmetric tridiagonal (float32 Sturm bisection)
+// ---------------------------------------------------------------------------
+__device__ int sturm_below(const float* a, const float* b2, int k, float x) {
+    int c = 0;
+    float d = a[0] - x;
+    if (d < 0.f) ++c;
+    for (int i = 1; i < k; ++i) {
+        if (d == 0.f) d = -1e-30f;
+        d = (a[i] - x) - b2[i - 1] / d;
+        if (d < 0.f) ++c;
+    }
+    return c;
+}
+
+// largest |eigenvalue| of T (alpha[0..k-1], beta[0..k-2]) in double units
+__device__ double tri_max_abs(const float* a, const float* b2, int k, double scale) {
+    float lo = -1.f, hi = 1.f;
+    // top eigenvalue: count(x) < k  <=>  x <= lambda_max
+    for (int it = 0; it < 26; ++it) {
+        float mid = 0.5f * (lo + hi);
+        if (sturm_below(a, b2, k, mid) < k) lo = mid; else hi = mid;
+    }
+    float top = 0.5f * (lo + hi);
+    lo = -1.f; hi = 1.f;
+    // bottom eigenvalue: count(x) >= 1  <=>  x > lambda_min
+    for (int it = 0; it < 26; ++it) {
+        float mid = 0.5f * (lo + hi);
+        if (sturm_below(a, b2, k, mid) >= 1) hi = mid; else lo = mid;
+    }
+    float bot = 0.5f * (lo + hi);
+    return scale * (double)fmaxf(fabsf(top), fabsf(bot));
+}
+
+// Lanczos with op = A^{-1} (inv = true) or A (inv = false) on augmented
+// vectors (m entries in a region + one border scalar).  Returns the extreme
+// |Ritz value|.  Requires L, ID, U (Phi^{-1} 1) and s.
+__device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool inv, double s) {
+    const int m = ly.m;
+    float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
+    double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX];
+    int qp = ly.Q0, q = ly.Q1, w = ly.Q2;
+    // start vector: cos(1.7 i + 0.3) + 0.1 on the n nodes and the border
+    double nrm2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double v = i < n ? cos(1.7 * i + 0.3) + 0.1 : 0.0;
+        S[q + i] = v;
+        S[qp + i] = 0.0;
+        nrm2 += v * v;
+    }
+    double qb = cos(1.7 * n + 0.3) + 0.1, qpb = 0.0;
+    nrm2 += qb * qb;
+    double inrm = rsqrt(nrm2);
+    for (int i = 0; i < n; ++i) S[q + i] *= inrm;
+    qb *= inrm;
+    double beta = 0.0, prev = -1.0, ext = 0.0;
+    for (int j = 0; j < LANCZOS_KMAX; ++j) {
+        double wb;
+        if (inv) {
+            // [c; d] = A^{-1} [f; g]: c0 = Phi^{-1} f, d = (1^T c0 - g) / s, c = c0 - d u
+            for (int i = 0; i < m; ++i) S[w + i] = S[q + i];
+            chol_solve(S, ly, w);
+            double sum = 0.0;
+            for (int i = 0; i < n; ++i) sum += S[w + i];
+            double d = (sum - qb) / s;
+            for (int i = 0; i < n; ++i) S[w + i] = fma(-d, S[ly.U + i], S[w + i]);
+            wb = d;
+        } else {
+            chol_mul(S, ly, q, w);
+            double sum = 0.0;
+            for (int i = 0; i < n; ++i) {
+                sum += S[q + i];
+                S[w + i] += qb;
+            }
+            wb = sum;
+        }
+        double a = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = fma(-beta, S[qp + i], S[w + i]);
+            S[w + i] = v;
+            a = fma(S[q + i], v, a);
+        }
+        wb = fma(-beta, qpb, wb);
+        a = fma(qb, wb, a);
+        double bn = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = fma(-a, S[q + i], S[w + i]);
+            S[w + i] = v;
+            bn = fma(v, v, bn);
+        }
+        wb = fma(-a, qb, wb);
+        bn = sqrt(fma(wb, wb, bn));
+        alpha_d[j] = a;
+        beta_d[j] = bn;
+        // scaled tridiagonal in float32 (Gershgorin bound as the scale)
+        double G = 0.0;
+        for (int i = 0; i <= j; ++i) {
+            double r = fabs(alpha_d[i]) + (i < j ? beta_d[i] : 0.0) + (i > 0 ? beta_d[i - 1] : 0.0);
+            G = fmax(G, r);
+        }
+        double ig = 1.0 / G;
+        for (int i = 0; i <= j; ++i) {
+            al[i] = (float)(alpha_d[i] * ig);
+            float bb = (float)(beta_d[i] * ig);
+            b2[i] = bb * bb;
+        }
+        ext = tri_max_abs(al, b2, j + 1, G);
+        if (j >= 1 && fabs(ext - prev) <= LANCZOS_RTOL * ext) break;
+        if (bn <= 1e-14 * fabs(a)) break;
+        prev = ext;
+        beta = bn;
+        double ib = 1.0 / bn;
+        int t = qp;
+        qp = q;
+        q = w;
+        w = t;
+        qpb = qb;
+        for (int i = 0; i < n; ++i) S[q + i] *= ib;
+        qb = wb * ib;
+    }
+    return ext;
+}
+
+// kappa_2(A(eps_s)); +inf when Phi is not numerically positive definite.
+__device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel, double eps_s) {
+    assemble_phi(S, ly, n, kernel, eps_s, ly.L, -1);
+    if (!cholesky(S, ly)) return INFINITY;
+    for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
+    chol_solve(S, ly, ly.U);
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += S[ly.U + i];
+    if (!(s > 0.0)) return INFINITY;
+    double tinv = lanczos_extreme(S, ly, n, true, s);
+    double lmax = lanczos_extreme(S, ly, n, false, s);
+    double k = lmax * tinv;
+    return isfinite(k) ? k : INFINITY;
+}
+
+// ---------------------------------------------------------------------------
+// per-lane root finder: secant bracketing then Brent-Dekker in x = ln eps_s
+// ---------------------------------------------------------------------------
+enum { PH_FIRST = 0, PH_BRACKET = 1, PH_BRENT = 2, PH_DONE = 3 };
+
+struct Search {
+    double x_next;               // point to evaluate next
+    double x0, f0;               // previous point while bracketing
+    double a, b, c, fa, fb, fc, d, e;   // Brent state (b: best)
+    double ka, kb, kc;                  // kappa at a, b, c
+    double xtol;
+    double k0;
+    int phase, evals, nbr;
+    int status;
+};
+
+__device__ inline double clampd(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
+
+// Brent-Dekker step after fb is known for b.  Returns true when converged.
+__device__ bool brent_step(Search& s) {
+    if ((s.fb > 0.0 && s.fc > 0.0) || (s.fb < 0.0 && s.fc < 0.0)) {
+        s.c = s.a;
+        s.fc = s.fa;
+        s.kc = s.ka;
+        s.d = s.e = s.b - s.a;
+    }
+    if (fabs(s.fc) < fabs(s.fb)) {
+        s.a = s.b; s.b = s.c; s.c = s.a;
+        s.fa = s.fb; s.fb = s.fc; s.fc = s.fa;
+        s.ka = s.kb; s.kb = s.kc; s.kc = s.ka;
+    }
+    const double u = 2.220446049250313e-16;
+    double tol1 = 2.0 * u * fabs(s.b) + 0.5 * s.xtol;
+    double mid = 0.5 * (s.c - s.b);
+    if (fabs(mid) <= tol1 || s.fb == 0.0) return true;
+    if (fabs(s.e) >= tol1 && fabs(s.fa) > fabs(s.fb)) {
+        double p, q, r;
+        double sr = s.fb / s.fa;
+        if (s.a == s.c) {
+            p = 2.0 * mid * sr;
+            q = 1.0 - sr;
+        } else {
+            q = s.fa / s.fc;
+            r = s.fb / s.fc;
+            p = sr * (2.0 * mid * q * (q - r) - (s.b - s.a) * (r - 1.0));
+            q = (q - 1.0) * (r - 1.0) * (sr - 1.0);
+        }
+        if (p > 0.0) q = -q; else p = -p;
+        if (2.0 * p < fmin(3.0 * mid * q - fabs(tol1 * q), fabs(s.e * q))) {
+            s.e = s.d;
+            s.d = p / q;
+        } else {
+            s.d = mid;
+            s.e = s.d;
+        }
+    } else {
+        s.d = mid;
+        s.e = s.d;
+    }
+    s.a = s.b;
+    s.fa = s.fb;
+    s.ka = s.kb;
+    s.b += fabs(s.d) > tol1 ? s.d : copysign(tol1, mid);
+    s.x_next = s.b;
+    return false;
+}
+
+__device__ void enter_brent(Search& s, double xl, double fl, double kl, double xr, double fr,
+                            double kr, double tol_s) {
+    s.a = xl; s.fa = fl; s.ka = kl;
+    s.b = xr; s.fb = fr; s.kb = kr;
+    s.c = s.a; s.fc = s.fa; s.kc = s.ka;
+    s.d = s.e = s.b - s.a;
+    s.xtol = tol_s / exp(fmax(xl, xr));
+    s.phase = PH_BRENT;
+}
+
+// Consume F(x_next) = f (kappa k).  Sets phase PH_DONE when finished.
+__device__ void search_update(Search& s, double f, double k, double tol_s, int max_evals,
+                              double acc_lo, double acc_hi, bool learned) {
+    s.evals++;
+    double x = s.x_next;
+    if (s.phase == PH_FIRST) {
+        if (learned && k >= acc_lo && k <= acc_hi) {
+            s.b = x; s.fb = f; s.kb = k;
+            s.status = RBFFD_STENCIL_ACCEPTED_PREDICTION;
+            s.phase = PH_DONE;
+            return;
+        }
+        s.x0 = x; s.f0 = f; s.k0 = k;
+        s.x_next = x + clampd(f / 8.0, -3.0, 3.0);
+        if (f == 0.0) {
+            s.b = x; s.kb = k; s.phase = PH_DONE;
+            return;
+        }
+        s.phase = PH_BRACKET;
+        s.nbr = 0;
+        return;
+    }
+    if (s.phase == PH_BRACKET) {
+        if ((f > 0.0) != (s.f0 > 0.0) || f == 0.0) {
+            if (f == 0.0) {
+                s.b = x; s.kb = k; s.phase = PH_DONE;
+                return;
+            }
+            // Brent from the bracket, with b at the newest point
+            enter_brent(s, s.x0, s.f0, s.k0, x, f, k, tol_s);
+            if (brent_step(s)) s.phase = PH_DONE;
+            return;
+        }
+        if (++s.nbr >= BRACKET_MAX || s.evals >= max_evals) {
+            s.status = RBFFD_STENCIL_NO_BRACKET;
+            s.b = x; s.kb = k; s.phase = PH_DONE;
+            return;
+        }
+        double slope = (f - s.f0) / (x - s.x0);
+        if (!(slope < -0.5) || !isfinite(slope)) slope = -8.0;
+        double step = clampd(-f / slope, -3.0, 3.0);
+        double dir = f > 0.0 ? 1.0 : -1.0;   // F decreases with x
+        if (step * dir < 0.05) step = 0.05 * dir;
+        s.x0 = x; s.f0 = f; s.k0 = k;
+        s.x_next = x + step;
+        return;
+    }
+    // Brent
+    s.fb = f;
+    s.kb = k;
+    if (s.evals >= max_evals) {
+        s.status = RBFFD_STENCIL_NO_CONVERGENCE;
+        s.phase = PH_DONE;
+        return;
+    }
+    if (brent_step(s)) s.phase = PH_DONE;
+}
+
+__device__ inline double F_of(double k, double kT) {
+    return isfinite(k) ? log(k / kT) : F_FAIL;
+}
+
+struct SearchArgs {
+    const double* X;
+    const int32_t* idx;
+    const int32_t* row_node;
+    GroupInfo gi;
+    double* scratch;
+    int lane_size;
+    int kernel;
+    double kT, tol, acc_lo, acc_hi;
+    int max_evals;
+    const float* guess_rows;     // ln(eps_s) per internal row, or NULL
+    unsigned long long* counters;  // per group
+    double* eps;
+    double* kappa;
+    int32_t* evals;
+    int32_t* status;
+};
+
+__global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
+    const int lane_id = threadIdx.x & 31;
+    const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    Lane S{A.scratch + warp_global * 32 * (int64_t)A.lane_size + lane_id};
+    int g = 0;
+    Layout ly = make_layout(A.gi.npad[0]);
+    bool have = false;
+    int64_t lr = 0, r = 0;
+    int n = A.gi.n[0];
+    Search st;
+    Geo geo;
+    geo.rs = 1.0;
+    double tol_s = 0.0;
+    bool learned = false;
+    while (true) {
+        if (!have) {
+            unsigned long long t = atomicAdd(&A.counters[g], 1ull);
+            int64_t cnt = A.gi.row_begin[g + 1] - A.gi.row_begin[g];
+            if ((int64_t)t < cnt) {
+                have = true;
+                lr = (int64_t)t;
+                r = A.gi.row_begin[g] + lr;
+                geo = load_geometry(S, ly, n, A.idx, A.gi.ell_off[g], A.gi.npad[g], lr, A.X, nullptr,
+                                    false);
+                tol_s = A.tol * geo.rs;
+                st.phase = PH_FIRST;
+                st.evals = 0;
+                st.status = RBFFD_STENCIL_OK;
+                float gs = A.guess_rows ? A.guess_rows[r] : NAN;
+                learned = isfinite(gs);
+                st.x_next = learned ? (double)gs : log(1.0 / geo.mean_d);
+            }
+        }
+        if (__ballot_sync(0xffffffffu, have) == 0) {
+            if (++g >= A.gi.ngroups) break;
+            ly = make_layout(A.gi.npad[g]);
+            n = A.gi.n[g];
+            continue;
+        }
+        if (have) {
+            double k = eval_kappa(S, ly, n, A.kernel, exp(st.x_next));
+            search_update(st, F_of(k, A.kT), k, tol_s, A.max_evals, A.acc_lo * A.kT, A.acc_hi * A.kT,
+                          learned);
+            if (st.phase == PH_DONE) {
+                int node = A.row_node[r];
+                A.eps[node] = exp(st.b) / geo.rs;
+                A.kappa[node] = st.kb;
+                A.evals[node] = st.evals;
+                A.status[node] = st.status;
+                have = false;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weights at a fixed eps per stencil
+// ---------------------------------------------------------------------------
+struct WeightArgs {
+    const double* X;
+    const double* NR;
+    const int32_t* idx;
+    const int32_t* row_node;
+    GroupInfo gi;
+    double* scratch;
+    int lane_size;
+    int kernel;
+    const double* eps_node;
+    double* w64;
+    float* w32;
+    int32_t* status;      // written only on failure
+    int* nfail;
+};
+
+// [c; d] = A^{-1} [f; 0] in place on region V (first n entries)
+__device__ void aug_solve0(const Lane& S, const Layout& ly, int n, int V, double s) {
+    chol_solve(S, ly, V);
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) sum += S[V + i];
+    double d = sum / s;
+    for (int i = 0; i < n; ++i) S[V + i] = fma(-d, S[ly.U + i], S[V + i]);
+}
+
+__global__ void __launch_bounds__(128) weights_kernel(WeightArgs A) {
+    const int lane_id = threadIdx.x & 31;
+    const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    Lane S{A.scratch + warp_global * 32 * (int64_t)A.lane_size + lane_id};
+    const int64_t R = A.gi.row_begin[A.gi.ngroups];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += stride) {
+        const int g = group_of_row(A.gi, r);
+        const int n = A.gi.n[g], npad = A.gi.npad[g];
+        const int64_t lr = r - A.gi.row_begin[g], off = A.gi.ell_off[g];
+        const Layout ly = make_layout(npad);
+        Geo geo = load_geometry(S, ly, n, A.idx, off, npad, lr, A.X, A.NR, true);
+        int node = A.row_node[r];
+        double eps_s = A.eps_node[node] * geo.rs;
+        double e2 = eps_s * eps_s;
+        assemble_phi(S, ly, n, A.kernel, eps_s, ly.L, ly.PH);
+        bool ok = cholesky(S, ly) && isfinite(eps_s) && eps_s > 0.0;
+        double s = 0.0;
+        if (ok) {
+            for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
+            chol_solve(S, ly, ly.U);
+            for (int i = 0; i < n; ++i) s += S[ly.U + i];
+            ok = s > 0.0 && isfinite(s);
+        }
+        if (!ok) {
+            A.status[node] = RBFFD_STENCIL_SINGULAR;
+            atomicAdd(A.nfail, 1);
+            for (int j = 0; j < npad; ++j) {
+                A.w64[ell_elem(off, npad, lr, j)] = 0.0;
+                A.w32[ell_elem(off, npad, lr, j)] = 0.f;
+            }
+            continue;
+        }
+        const int XS = ly.XS, m = ly.m;
+        // centre projector P_0 = I - n_0 n_0^T; rhs_d,j = psi(r_0j) [P_0 (x_0 - x_j)]_d
+        double n0x = S[ly.NS], n0y = S[ly.NS + m], n0z = S[ly.NS + 2 * m];
+        for (int d = 0; d < 3; ++d)
+            for (int i = 0; i < m; ++i) S[ly.GV + d * m + i] = 0.0;
+        for (int j = 1; j < n; ++j) {
+            double ph = S[ly.PH + pk(j, 0)];
+            double ps = psi_from_phi(A.kernel, e2, ph);
+            double dx = -S[XS + j], dy = -S[XS + m + j], dz = -S[XS + 2 * m + j];   // x_0 - x_j
+            double nd = n0x * dx + n0y * dy + n0z * dz;
+            S[ly.GV + j] = ps * (dx - n0x * nd);
+            S[ly.GV + m + j] = ps * (dy - n0y * nd);
+            S[ly.GV + 2 * m + j] = ps * (dz - n0z * nd);
+        }
+        for (int d = 0; d < 3; ++d) aug_solve0(S, ly, n, ly.GV + d * m, s);
+        // h_i = P_i g_i
+        for (int i = 0; i < n; ++i) {
+            double gx = S[ly.GV + i], gy = S[ly.GV + m + i], gz = S[ly.GV + 2 * m + i];
+            double nx = S[ly.NS + i], ny = S[ly.NS + m + i], nz = S[ly.NS + 2 * m + i];
+            double nd = nx * gx + ny * gy + nz * gz;
+            S[ly.HV + i] = gx - nx * nd;
+            S[ly.HV + m + i] = gy - ny * nd;
+            S[ly.HV + 2 * m + i] = gz - nz * nd;
+        }
+        // v_j = sum_i psi_ij (x_i - x_j) . h_i   (v in region T0... use Q0)
+        const int V = ly.Q0;
+        for (int i = 0; i < m; ++i) S[V + i] = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double xi = S[XS + i], yi = S[XS + m + i], zi = S[XS + 2 * m + i];
+            double hx = S[ly.HV + i], hy = S[ly.HV + m + i], hz = S[ly.HV + 2 * m + i];
+            double vi = 0.0;
+            int base = pk(i, 0);
+            for (int j = 0; j < i; ++j) {
+                double ps = psi_from_phi(A.kernel, e2, S[ly.PH + base + j]);
+                double dx = xi - S[XS + j], dy = yi - S[XS + m + j], dz = zi - S[XS + 2 * m + j];
+                double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
+                // pair (i, j): v_j += psi (x_i - x_j) . h_i ; v_i += psi (x_j - x_i) . h_j
+                S[V + j] = fma(ps, dx * hx + dy * hy + dz * hz, S[V + j]);
+                vi = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi);
+            }
+            S[V + i] += vi;
+        }
+        aug_solve0(S, ly, n, V, s);
+        double inv_rs2 = 1.0 / (geo.rs * geo.rs);
+        for (int j = 0; j < npad; ++j) {
+            double w = j < n ? S[V + j] * inv_rs2 : 0.0;
+            A.w64[ell_elem(off, npad, lr, j)] = w;
+            A.w32[ell_elem(off, npad, lr, j)] = (float)w;
+        }
+    }
+}
+
+struct LaunchShape {
+    int threads, blocks;
+};
+
+LaunchShape launch_shape(const rbffd_build_opts& o, int64_t rows) {
+    LaunchShape ls;
+    ls.threads = o.block_threads > 0 ? o.block_threads : 128;
+    int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 2;
+    int64_t want = (int64_t)sm_count() * bps;
+    int64_t need = (rows + ls.threads - 1) / ls.threads;
+    ls.blocks = (int)std::max<int64_t>(1, std::min(want, need));
+    return ls;
+}
+
+}  // namespace
+
+rbffd_status build_search(rbffd_op* op, const double* nodes, const double* normals,
+                          const rbffd_build_opts& o, const float* guess_rows, cudaStream_t st) {
+    (void)normals;
+    const GroupInfo& gi = op->gi;
+    int mmax = 0;
+    for (int g = 0; g < gi.ngroups; ++g) mmax = std::max(mmax, gi.npad[g]);
+    Layout ly = make_layout(mmax);
+    LaunchShape ls = launch_shape(o, op->N);
+    RBFFD_CHECK_ARG(ls.threads % 32 == 0 && ls.threads <= 128, "block_threads must be 32..128, x32");
+    int64_t lanes = (int64_t)ls.blocks * ls.threads;
+    double* scratch = nullptr;
+    unsigned long long* ctr = nullptr;
+    RBFFD_CUDA_TRY(cudaMallocAsync(&scratch, (size_t)lanes * ly.size * sizeof(double), st));
+    RBFFD_CUDA_TRY(cudaMallocAsync(&ctr, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
+    RBFFD_CUDA_TRY(cudaMemsetAsync(ctr, 0, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
+    SearchArgs A;
+    A.X = nodes;
+    A.idx = op->idx;
+    A.row_node = op->row_node;
+    A.gi = gi;
+    A.scratch = scratch;
+    A.lane_size = ly.size;
+    A.kernel = o.kernel;
+    A.kT = o.kappa_target;
+    A.tol = o.eps_tol;
+    A.acc_lo = o.accept_lo;
+    A.acc_hi = o.accept_hi;
+    A.max_evals = o.max_evals;
+    A.guess_rows = guess_rows;
+    A.counters = ctr;
+    A.eps = op->eps;
+    A.kappa = op->kappa;
+    A.evals = op->evals;
+    A.status = op->status;
+    search_kernel<<<ls.blocks, ls.threads, 0, st>>>(A);
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    RBFFD_CUDA_TRY(cudaFreeAsync(scratch, st));
+    RBFFD_CUDA_TRY(cudaFreeAsync(ctr, st));
+    return RBFFD_OK;
+}
+
+rbffd_status build_weights(rbffd_op* op, const double* nodes, const double* normals,
+                           const rbffd_build_opts& o, const double* eps_node, cudaStream_t st) {
+    const GroupInfo& gi = op->gi;
+    int mmax = 0;
+    for (int g = 0; g < gi.ngroups; ++g) mmax = std::max(mmax, gi.npad[g]);
+    Layout ly = make_layout(mmax);
+    LaunchShape ls = launch_shape(o, op->N);
+    RBFFD_CHECK_ARG(ls.threads % 32 == 0 && ls.threads <= 128, "block_threads must be 32..128, x32");
+    int64_t lanes = (int64_t)ls.blocks * ls.threads;
+    double* scratch = nullptr;
+    int* nfail = nullptr;
+    RBFFD_CUDA_TRY(cudaMallocAsync(&scratch, (size_t)lanes * ly.size * sizeof(double), st));
+    RBFFD_CUDA_TRY(cudaMallocAsync(&nfail, sizeof(int), st));
+    RBFFD_CUDA_TRY(cudaMemsetAsync(nfail, 0, sizeof(int), st));
+    WeightArgs A;
+    A.X = nodes;
+    A.NR = normals;
+    A.idx = op->idx;
+    A.row_node = op->row_node;
+    A.gi = gi;
+    A.scratch = scratch;
+    A.lane_size = ly.size;
+    A.kernel = o.kernel;
+    A.eps_node = eps_node;
+    A.w64 = op->w64;
+    A.w32 = op->w32;
+    A.status = op->status;
+    A.nfail = nfail;
+    weights_kernel<<<ls.blocks, ls.threads, 0, st>>>(A);
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    int hf = 0;
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(&hf, nfail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    RBFFD_CUDA_TRY(cudaFreeAsync(scratch, st));
+    RBFFD_CUDA_TRY(cudaFreeAsync(nfail, st));
+    if (hf) {
+        set_error("%d stencils have a local matrix that is not numerically positive definite", hf);
+        return RBFFD_ESINGULAR;
+    }
+    return RBFFD_OK;
+}
+
+}  // namespace rbffd

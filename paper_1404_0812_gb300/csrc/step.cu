@@ -1,0 +1,603 @@
+// IMEX method-of-lines stepping (Section 4.2 method of lines; Section 7
+// SBDF2 with the diffusion implicit; BiCGSTAB as Section 4.2 / Section 6 use).
+//
+//   d/dt u = delta_u L u + f(u, v),  d/dt v = delta_v L v + g(u, v)
+//   SBDF2:  (3 I - 2 dt delta L) u^{n+1} = 4 u^n - u^{n-1} + 2 dt (2 f^n - f^{n-1})
+//   first step without history: (I - dt delta L) u^1 = u^0 + dt f^0
+//
+// GPU design: one cooperative persistent launch per time step.  Every
+// thread owns a fixed set of operator rows for the whole step; both species
+// are solved together so each pass over the ELL matrix (the bytes that
+// bound the step) serves two SpMVs.  Phases of BiCGSTAB are separated by a
+// grid barrier of our own with a bounded spin (a block that waits longer
+// than about a second sets an error flag and leaves, so nothing can hang);
+// dot products are reduced per block in float64, written to per-phase
+// slots, and every block sums the slots in the same fixed order, so all
+// blocks hold bit-identical scalars.  Vectors written inside the launch are
+// read with L1-bypassing loads.  The solution is updated in place in u
+// (after the right-hand side is formed, u is only read by its own row).
+// The launch can be captured once into a CUDA graph and replayed per step.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+struct rbffd_step_ws {
+    int dtype;
+    int64_t N;
+    size_t elem;
+    void* vec;                     // 2 species x 7 vectors (b, r, rh, p, q, s, t)
+    double* partial;               // phases x blocks x 8
+    unsigned long long* bar;       // barrier counter
+    int* flags;                    // [0] error (timeout), [1] not converged, [2] has_history
+    int* rep;                      // per step: iters_u, iters_v, failed
+    double* rep_res;               // per step: relres_u, relres_v
+    int64_t rep_cap;
+    int blocks, threads;
+    cudaGraphExec_t graph;
+    const void* graph_key[8];
+    bool graph_ok;
+};
+
+namespace rbffd {
+
+void step_ws_free(rbffd_step_ws* ws) {
+    if (!ws) return;
+    cudaFree(ws->vec);
+    cudaFree(ws->partial);
+    cudaFree(ws->bar);
+    cudaFree(ws->flags);
+    cudaFree(ws->rep);
+    cudaFree(ws->rep_res);
+    if (ws->graph) cudaGraphExecDestroy(ws->graph);
+    delete ws;
+}
+
+namespace {
+
+constexpr int NPHASE = 6;
+constexpr int NSLOT = 8;
+constexpr long long MAX_POLLS = 20000000;   // ~1-2 s with 32 ns sleeps
+
+template <typename T>
+struct Args {
+    const int32_t* idx;
+    const T* w;
+    const int32_t* row_node;
+    GroupInfo gi;
+    int64_t N;
+    T *u, *v, *up, *vp, *fp, *gp;
+    T* vec;            // 2 x 7 x N
+    int ns;
+    int model;
+    T c[8];
+    T dt;
+    T delta[2];
+    double tol;
+    int maxit;
+    double* partial;
+    unsigned long long* bar;
+    int* flags;
+    int* rep;
+    double* rep_res;
+    int64_t rep_slot;
+};
+
+enum { VB = 0, VR = 1, VRH = 2, VP = 3, VQ = 4, VS = 5, VT = 6 };
+
+template <typename T>
+__device__ __forceinline__ T* V(const Args<T>& a, int sp, int k) {
+    return a.vec + ((int64_t)sp * 7 + k) * a.N;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+
+// bounded grid barrier: the target grows by gridDim.x per call
+__device__ bool grid_sync(unsigned long long* bar, unsigned long long target, int* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1ull);
+        long long polls = 0;
+        while (*((volatile unsigned long long*)bar) < target) {
+            if (++polls > MAX_POLLS || *((volatile int*)err)) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// block-reduce K doubles into partial[phase][block][0..K-1]
+template <int K>
+__device__ void block_partial(double (&v)[K], double* partial, int phase) {
+    __shared__ double sh[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
+        partial[((int64_t)phase * gridDim.x + blockIdx.x) * NSLOT + threadIdx.x] = s;
+    }
+}
+
+// every block sums the per-block partials of a phase in block order
+template <int K>
+__device__ void grid_total(const double* partial, int phase, double (&out)[K]) {
+    __shared__ double tot[K];
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b)
+            s += __ldcg(partial + ((int64_t)phase * gridDim.x + b) * NSLOT + threadIdx.x);
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = tot[k];
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void react(const Args<T>& a, T u, T v, T& f, T& g) {
+    switch (a.model) {
+        case RBFFD_MODEL_LINEAR: f = a.c[0] * u; g = a.c[1] * v; break;
+        case RBFFD_MODEL_SCHNAKENBERG: {
+            T uuv = u * u * v;
+            f = a.c[2] * (a.c[0] - u + uuv);
+            g = a.c[2] * (a.c[1] - uuv);
+        } break;
+        case RBFFD_MODEL_GRAY_SCOTT: {
+            T uvv = u * v * v;
+            f = -uvv + a.c[0] * (T(1) - u);
+            g = uvv - (a.c[0] + a.c[1]) * v;
+        } break;
+        case RBFFD_MODEL_BARRIO: {   // Eqs. turing1, turing2
+            T al = a.c[0], be = a.c[1], ga = a.c[2], t1 = a.c[3], t2 = a.c[4];
+            f = al * u * (T(1) - t1 * v * v) + v * (T(1) - t2 * u);
+            g = be * v * (T(1) + (al * t1 / be) * u * v) + u * (ga + t2 * v);
+        } break;
+        default: f = T(0); g = T(0);
+    }
+}
+
+// (L x0)_row and (L x1)_row in one pass over the row (x read L1-bypassing)
+template <typename T>
+__device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, const T* x0, const T* x1, bool two,
+                                       T& y0, T& y1) {
+    int g = group_of_row(a.gi, r);
+    const int npad = a.gi.npad[g];
+    const int64_t base = ell_elem(a.gi.ell_off[g], npad, r - a.gi.row_begin[g], 0);
+    T s0 = T(0), s1 = T(0);
+    for (int jb = 0; jb < npad; jb += 4) {
+        const int64_t e = base + (int64_t)(jb >> 2) * 128;
+        int4 iv = __ldg(reinterpret_cast<const int4*>(a.idx + e));
+        int ii[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T w = __ldg(a.w + e + q);
+            s0 = fma(w, ldcg(x0 + ii[q]), s0);
+            if (two) s1 = fma(w, ldcg(x1 + ii[q]), s1);
+        }
+    }
+    y0 = s0;
+    y1 = s1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool two = a.ns == 2;
+    const bool hist = *((volatile int*)(a.flags + 2)) != 0;
+    unsigned long long target = 0;
+    const T c0 = hist ? T(3) : T(1);
+    const T cl = hist ? T(2) * a.dt : a.dt;
+    const T k0 = cl * a.delta[0], k1 = cl * a.delta[1];
+    T* u = a.u;
+    T* v = two ? a.v : nullptr;
+
+    // ---- phase R: reaction, right-hand side, r0 = b - A u, history rotation
+    {
+        double d[6] = {0, 0, 0, 0, 0, 0};   // |b|^2, |r|^2, (rh, r) per species
+        for (int64_t r = t0; r < a.N; r += stride) {
+            int i = a.row_node[r];
+            T Lu, Lv;
+            row_L2(a, r, u, v, two, Lu, Lv);
+            T ui = u[i], vi = two ? v[i] : T(0);
+            T f, g;
+            react(a, ui, vi, f, g);
+            T bu, bv = T(0);
+            if (hist) {
+                bu = T(4) * ui - a.up[i] + T(2) * a.dt * (T(2) * f - a.fp[i]);
+                if (two) bv = T(4) * vi - a.vp[i] + T(2) * a.dt * (T(2) * g - a.gp[i]);
+            } else {
+                bu = ui + a.dt * f;
+                if (two) bv = vi + a.dt * g;
+            }
+            a.up[i] = ui;
+            a.fp[i] = f;
+            T ru = bu - (c0 * ui - k0 * Lu);
+            V(a, 0, VB)[i] = bu;
+            V(a, 0, VR)[i] = ru;
+            V(a, 0, VRH)[i] = ru;
+            V(a, 0, VP)[i] = T(0);
+            V(a, 0, VQ)[i] = T(0);
+            d[0] += (double)bu * bu;
+            d[1] += (double)ru * ru;
+            if (two) {
+                a.vp[i] = vi;
+                a.gp[i] = g;
+                T rv = bv - (c0 * vi - k1 * Lv);
+                V(a, 1, VB)[i] = bv;
+                V(a, 1, VR)[i] = rv;
+                V(a, 1, VRH)[i] = rv;
+                V(a, 1, VP)[i] = T(0);
+                V(a, 1, VQ)[i] = T(0);
+                d[3] += (double)bv * bv;
+                d[4] += (double)rv * rv;
+            }
+        }
+        block_partial<6>(d, a.partial, 0);
+    }
+    if (!grid_sync(a.bar, target += gridDim.x, a.flags)) return;
+    double tot[6];
+    grid_total<6>(a.partial, 0, tot);
+
+    double bnorm[2] = {sqrt(tot[0]), sqrt(tot[3])};
+    double rho[2] = {tot[1], tot[4]};    // (rh, r0) = |r0|^2
+    double rho_prev[2] = {1.0, 1.0}, alpha[2] = {1.0, 1.0}, omega[2] = {1.0, 1.0};
+    bool active[2], conv[2] = {false, false}, fail[2] = {false, false};
+    int iters[2] = {0, 0};
+    double relres[2];
+    for (int k = 0; k < 2; ++k) {
+        bool exists = k == 0 || two;
+        relres[k] = bnorm[k] > 0 ? sqrt(rho[k]) / bnorm[k] : 0.0;
+        conv[k] = !exists || bnorm[k] == 0.0 || relres[k] <= a.tol;
+        active[k] = !conv[k];
+    }
+    if (bnorm[0] == 0.0)   // b = 0: x = 0
+        for (int64_t r = t0; r < a.N; r += stride) u[a.row_node[r]] = T(0);
+    if (two && bnorm[1] == 0.0)
+        for (int64_t r = t0; r < a.N; r += stride) v[a.row_node[r]] = T(0);
+
+    int it = 0;
+    while ((active[0] || active[1]) && it < a.maxit) {
+        ++it;
+        // ---- A: p = r + beta (p - omega q)
+        double beta[2];
+        for (int k = 0; k < 2; ++k) {
+            beta[k] = (rho[k] / rho_prev[k]) * (alpha[k] / omega[k]);
+            if (active[k] && (rho[k] == 0.0 || !isfinite(beta[k]))) {
+                fail[k] = true;
+                active[k] = false;
+            }
+        }
+        for (int64_t r = t0; r < a.N; r += stride) {
+            int i = a.row_node[r];
+            for (int k = 0; k < 2; ++k) {
+                if (!active[k]) continue;
+                T* p = V(a, k, VP);
+                p[i] = V(a, k, VR)[i] + (T)beta[k] * (p[i] - (T)omega[k] * V(a, k, VQ)[i]);
+            }
+        }
+        if (!grid_sync(a.bar, target += gridDim.x, a.flags)) return;
+        // ---- B: q = A p ; (rh, q)
+        {
+            double d[2] = {0, 0};
+            for (int64_t r = t0; r < a.N; r += stride) {
+                int i = a.row_node[r];
+                T L0, L1;
+                row_L2(a, r, V(a, 0, VP), two ? V(a, 1, VP) : nullptr, two && active[1], L0, L1);
+                if (active[0]) {
+                    T q = c0 * V(a, 0, VP)[i] - k0 * L0;
+                    V(a, 0, VQ)[i] = q;
+                    d[0] += (double)V(a, 0, VRH)[i] * q;
+                }
+                if (active[1]) {
+                    T q = c0 * V(a, 1, VP)[i] - k1 * L1;
+                    V(a, 1, VQ)[i] = q;
+                    d[1] += (double)V(a, 1, VRH)[i] * q;
+                }
+            }
+            block_partial<2>(d, a.partial, 1);
+        }
+        if (!grid_sync(a.bar, target += gridDim.x, a.flags)) return;
+        {
+            double s[2];
+            grid_total<2>(a.partial, 1, s);
+            for (int k = 0; k < 2; ++k) {
+                if (!active[k]) continue;
+                alpha[k] = rho[k] / s[k];
+                if (s[k] == 0.0 || !isfinite(alpha[k])) {
+                    fail[k] = true;
+                    active[k] = false;
+                }
+            }
+        }
+        // ---- C: s = r - alpha q ; |s|^2
+        {
+            double d[2] = {0, 0};
+            for (int64_t r = t0; r < a.N; r += stride) {
+                int i = a.row_node[r];
+                for (int k = 0; k < 2; ++k) {
+                    if (!active[k]) continue;
+                    T s = V(a, k, VR)[i] - (T)alpha[k] * V(a, k, VQ)[i];
+                    V(a, k, VS)[i] = s;
+                    d[k] += (double)s * s;
+                }
+            }
+            block_partial<2>(d, a.partial, 2);
+        }
+        if (!grid_sync(a.bar, target += gridDim.x, a.flags)) return;
+        bool early[2] = {false, false};
+        {
+            double s[2];
+            grid_total<2>(a.partial, 2, s);
+            for (int k = 0; k < 2; ++k) {
+                if (!active[k]) continue;
+                double rr = sqrt(s[k]) / bnorm[k];
+                if (rr <= a.tol) {
+                    early[k] = true;
+                    relres[k] = rr;
+                }
+            }
+        }
+        // ---- D: t = A s ; (t, s), (t, t)   (x += alpha p where s converged)
+        {
+            double d[4] = {0, 0, 0, 0};
+            bool need0 = active[0] && !early[0], need1 = active[1] && !early[1];
+            for (int64_t r = t0; r < a.N; r += stride) {
+                int i = a.row_node[r];
+                T L0 = T(0), L1 = T(0);
+                if (need0 || need1)
+                    row_L2(a, r, V(a, 0, VS), two ? V(a, 1, VS) : nullptr, two && need1, L0, L1);
+                for (int k = 0; k < 2; ++k) {
+                    T* x = k == 0 ? u : v;
+                    if (early[k]) {
+                        x[i] += (T)alpha[k] * V(a, k, VP)[i];
+                    } else if (active[k]) {
+                        T s = V(a, k, VS)[i];
+                        T t = c0 * s - (k == 0 ? k0 * L0 : k1 * L1);
+                        V(a, k, VT)[i] = t;
+                        d[2 * k] += (double)t * s;
+                        d[2 * k + 1] += (double)t * t;
+                    }
+                }
+            }
+            block_partial<4>(d, a.partial, 3);
+        }
+        for (int k = 0; k < 2; ++k)
+            if (early[k]) {
+                active[k] = false;
+                conv[k] = true;
+                iters[k] = it;
+            }
+        if (!grid_sync(a.bar, target += gridDim.x, a.flags)) return;
+        {
+            double s[4];
+            grid_total<4>(a.partial, 3, s);
+            for (int k = 0; k < 2; ++k) {
+                if (!active[k]) continue;
+                omega[k] = s[2 * k] / s[2 * k + 1];
+                if (s[2 * k + 1] == 0.0 || !isfinite(omega[k])) {
+                    fail[k] = true;
+                    active[k] = false;
+                }
+            }
+        }
+        // ---- E: x += alpha p + omega s ; r = s - omega t ; (rh, r), |r|^2
+        {
+            double d[4] = {0, 0, 0, 0};
+            for (int64_t r = t0; r < a.N; r += stride) {
+                int i = a.row_node[r];
+                for (int k = 0; k < 2; ++k) {
+                    if (!active[k]) continue;
+                    T* x = k == 0 ? u : v;
+                    T s = V(a, k, VS)[i];
+                    x[i] += (T)alpha[k] * V(a, k, VP)[i] + (T)omega[k] * s;
+                    T rn = s - (T)omega[k] * V(a, k, VT)[i];
+                    V(a, k, VR)[i] = rn;
+                    d[2 * k] += (double)V(a, k, VRH)[i] * rn;
+                    d[2 * k + 1] += (double)rn * rn;
+                }
+            }
+            block_partial<4>(d, a.partial, 4);
+        }
+        if (!grid_sync(a.bar, target += gridDim.x, a.flags)) return;
+        {
+            double s[4];
+            grid_total<4>(a.partial, 4, s);
+            for (int k = 0; k < 2; ++k) {
+                if (!active[k]) continue;
+                rho_prev[k] = rho[k];
+                rho[k] = s[2 * k];
+                relres[k] = sqrt(s[2 * k + 1]) / bnorm[k];
+                if (relres[k] <= a.tol) {
+                    active[k] = false;
+                    conv[k] = true;
+                    iters[k] = it;
+                } else if (omega[k] == 0.0) {
+                    fail[k] = true;
+                    active[k] = false;
+                }
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bool bad = false;
+        for (int k = 0; k < 2; ++k) {
+            if (active[k]) {   // hit maxit
+                iters[k] = it;
+                bad = true;
+            }
+            if (fail[k]) bad = true;
+        }
+        int* rp = a.rep + a.rep_slot * 3;
+        rp[0] = iters[0];
+        rp[1] = iters[1];
+        rp[2] = bad ? 1 : 0;
+        a.rep_res[a.rep_slot * 2] = relres[0];
+        a.rep_res[a.rep_slot * 2 + 1] = relres[1];
+        if (bad) atomicExch(a.flags + 1, 1);
+        a.flags[2] = 1;   // history exists from now on
+    }
+}
+
+template <typename T>
+void fill_args(Args<T>& a, rbffd_op* op, rbffd_state* s, const rbffd_step_params* p, rbffd_step_ws* ws) {
+    a.idx = op->idx;
+    a.w = std::is_same<T, float>::value ? (const T*)op->w32 : (const T*)op->w64;
+    a.row_node = op->row_node;
+    a.gi = op->gi;
+    a.N = op->N;
+    a.u = (T*)s->u;
+    a.v = (T*)s->v;
+    a.up = (T*)s->u_prev;
+    a.vp = (T*)s->v_prev;
+    a.fp = (T*)s->f_prev;
+    a.gp = (T*)s->g_prev;
+    a.vec = (T*)ws->vec;
+    a.ns = p->nspecies;
+    a.model = p->model;
+    for (int i = 0; i < 8; ++i) a.c[i] = (T)p->coef[i];
+    a.dt = (T)p->dt;
+    a.delta[0] = (T)p->delta_u;
+    a.delta[1] = (T)p->delta_v;
+    a.tol = p->tol;
+    a.maxit = p->maxit;
+    a.partial = ws->partial;
+    a.bar = ws->bar;
+    a.flags = ws->flags;
+    a.rep = ws->rep;
+    a.rep_res = ws->rep_res;
+    a.rep_slot = 0;
+}
+
+template <typename T>
+rbffd_status launch_step(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
+    RBFFD_CUDA_TRY(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned long long), st));
+    void* args[] = {&a};
+    RBFFD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)step_kernel<T>, dim3(ws->blocks),
+                                               dim3(ws->threads), args, 0, st));
+    return RBFFD_OK;
+}
+
+}  // namespace
+}  // namespace rbffd
+
+using namespace rbffd;
+
+extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbffd_step_params* p,
+                                        int64_t nsteps, void* stream, rbffd_step_report* report) {
+    RBFFD_CHECK_ARG(op && s && p, "NULL argument");
+    RBFFD_CHECK_ARG(p->dtype == RBFFD_F32 || p->dtype == RBFFD_F64, "dtype");
+    RBFFD_CHECK_ARG(p->nspecies == 1 || p->nspecies == 2, "nspecies must be 1 or 2");
+    RBFFD_CHECK_ARG(s->u && s->u_prev && s->f_prev, "u / u_prev / f_prev are NULL");
+    RBFFD_CHECK_ARG(p->nspecies == 1 || (s->v && s->v_prev && s->g_prev), "v state is NULL");
+    RBFFD_CHECK_ARG(p->dt > 0 && p->tol > 0 && p->maxit > 0 && nsteps >= 0, "dt / tol / maxit / nsteps");
+    RBFFD_CHECK_ARG(p->model >= RBFFD_MODEL_NONE && p->model <= RBFFD_MODEL_BARRIO, "model");
+    RBFFD_CHECK_ARG(p->model != RBFFD_MODEL_BARRIO || p->coef[1] != 0.0, "Barrio model needs beta != 0");
+    cudaStream_t st = as_stream(stream);
+    const size_t elem = p->dtype == RBFFD_F32 ? 4 : 8;
+    rbffd_step_ws* ws = op->step;
+    if (ws && ws->elem != elem) {
+        step_ws_free(ws);
+        ws = op->step = nullptr;
+    }
+    if (!ws) {
+        ws = new rbffd_step_ws();
+        memset(ws, 0, sizeof(*ws));
+        op->step = ws;
+        ws->elem = elem;
+        ws->N = op->N;
+        ws->threads = 256;
+        int dev = 0, per_sm = 0;
+        RBFFD_CUDA_TRY(cudaGetDevice(&dev));
+        if (elem == 4)
+            RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<float>, 256, 0));
+        else
+            RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<double>, 256, 0));
+        int64_t maxb = (int64_t)std::max(1, per_sm) * sm_count();
+        int64_t want = (op->N + 4 * 256 - 1) / (4 * 256);   // at least ~4 rows per thread
+        ws->blocks = (int)std::max<int64_t>(1, std::min(maxb, std::max<int64_t>(want, 1)));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->vec, 2 * 7 * op->N * elem));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->partial, (size_t)NPHASE * ws->blocks * NSLOT * sizeof(double)));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->bar, sizeof(unsigned long long)));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->flags, 4 * sizeof(int)));
+        ws->rep_cap = 0;
+    }
+    if (ws->rep_cap < std::max<int64_t>(nsteps, 1)) {
+        cudaFree(ws->rep);
+        cudaFree(ws->rep_res);
+        ws->rep_cap = std::max<int64_t>(nsteps, 1);
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->rep, ws->rep_cap * 3 * sizeof(int)));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->rep_res, ws->rep_cap * 2 * sizeof(double)));
+    }
+    int hflags[4] = {0, 0, s->has_history ? 1 : 0, 0};
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, st));
+    RBFFD_CUDA_TRY(cudaMemsetAsync(ws->rep, 0, ws->rep_cap * 3 * sizeof(int), st));
+    rbffd_status rs = RBFFD_OK;
+    for (int64_t k = 0; k < nsteps && rs == RBFFD_OK; ++k) {
+        if (elem == 4) {
+            Args<float> a;
+            fill_args(a, op, s, p, ws);
+            a.rep_slot = k;
+            rs = launch_step(a, ws, st);
+        } else {
+            Args<double> a;
+            fill_args(a, op, s, p, ws);
+            a.rep_slot = k;
+            rs = launch_step(a, ws, st);
+        }
+    }
+    if (rs != RBFFD_OK) return rs;
+    std::vector<int> rep(std::max<int64_t>(nsteps, 1) * 3);
+    std::vector<double> res(std::max<int64_t>(nsteps, 1) * 2);
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(hflags, ws->flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+    if (nsteps > 0) {
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(rep.data(), ws->rep, nsteps * 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(res.data(), ws->rep_res, nsteps * 2 * sizeof(double),
+                                       cudaMemcpyDeviceToHost, st));
+    }
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    rbffd_step_report r;
+    memset(&r, 0, sizeof(r));
+    r.failed_step = -1;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        r.max_iters_u = std::max(r.max_iters_u, rep[3 * k]);
+        r.max_iters_v = std::max(r.max_iters_v, rep[3 * k + 1]);
+        r.total_iters += rep[3 * k] + rep[3 * k + 1];
+        if (rep[3 * k + 2] && r.failed_step < 0) r.failed_step = s->step + k;
+        r.last_relres_u = res[2 * k];
+        r.last_relres_v = res[2 * k + 1];
+    }
+    r.steps_done = nsteps;
+    if (nsteps > 0) s->has_history = 1;
+    s->step += nsteps;
+    if (report) *report = r;
+    if (hflags[0]) {
+        set_error("grid barrier timed out (blocks not co-resident?)");
+        return RBFFD_TIMEOUT;
+    }
+    if (hflags[1]) {
+        set_error("BiCGSTAB failed at step %lld", (long long)r.failed_step);
+        return RBFFD_SOLVER_NOT_CONVERGED;
+    }
+    return RBFFD_OK;
+}

@@ -1,0 +1,183 @@
+"""GPU parity of the operator build (stencils, shape parameters, weights) and
+of the apply, through the C ABI, against the CPU oracle.
+
+Tolerances (floating point; derived in the design doc from the arithmetic):
+* applied operator, smooth u: ||L_gpu u - L_cpu u||_inf / ||L_cpu u||_inf
+  <= 1e-8 (also at kappa_T = 1e12);
+* applied operator, random u at kappa_T = 1e12: <= 5e-5 -- two exact-in-
+  exact-arithmetic float64 orderings of the same weights already differ by
+  3.5e-6 there (kappa_T * unit roundoff amplification), so the bound is 15x
+  that spread; at kappa <= 1e8 random u is held to 1e-8;
+* stencil indices: bit-exact (the (d^2, index) key is bit-reproducible);
+* eps: |eps_gpu - eps_cpu| <= 2 * tol + 1e-5 * eps (both searches stop
+  within tol of the root; the root itself moves with kappa's float64 noise).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import operator as oop
+from oracle import stencils as ost
+from oracle import weights as ow
+from paper_1404_0812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def T(a, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def rel_inf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1404_0812_gb300 as R
+    R._lib.load()
+    return R
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    ns = W.icosahedral_sphere(4)
+    ref = oop.build_operator(ns.X, ns.normals, 31, ow.GAUSSIAN, kappa_T=1e12)
+    return ns, ref
+
+
+def test_stencils_bit_exact(R, sphere):
+    ns, ref = sphere
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="gaussian", eps_override=T(ref.eps))
+    idx, _ = R.get_rows(op)
+    assert np.array_equal(idx.cpu().numpy(), ref.idx.astype(np.int32))
+    assert op.nnz == 31 * ns.N
+
+
+def test_weights_at_oracle_eps(R, sphere):
+    ns, ref = sphere
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="gaussian", eps_override=T(ref.eps))
+    u_s = W.sph_harm_y32(ns.X)
+    u_r = W.uniform_field(ns.N, seed=1)
+    y_s = R.apply(op, T(u_s)).cpu().numpy()
+    y_r = R.apply(op, T(u_r)).cpu().numpy()
+    assert rel_inf(y_s, oop.apply(ref, u_s)) <= 1e-8
+    assert rel_inf(y_r, oop.apply(ref, u_r)) <= 5e-5
+    # float32 apply of the float32 weights against the float64 oracle
+    y32 = R.apply(op, T(u_s, torch.float32)).cpu().numpy().astype(np.float64)
+    assert rel_inf(y32, oop.apply(ref, u_s)) <= 1e-3
+    _, w = R.get_rows(op)
+    w = w.cpu().numpy()
+    assert np.abs(w.sum(axis=1)).max() <= 1e-9 * np.abs(w).sum(axis=1).max()
+
+
+def test_eps_search_matches_oracle(R, sphere):
+    ns, ref = sphere
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="gaussian", kappa_target=1e12)
+    info = {k: v.cpu().numpy() for k, v in R.get_stencil_info(op).items()}
+    assert np.all(info["status"] == 0)
+    d = np.abs(info["eps"] - ref.eps)
+    assert np.all(d <= 2e-4 + 1e-5 * ref.eps), d.max()
+    assert np.all(np.abs(np.log(info["kappa"] / 1e12)) < 0.05)
+    assert np.all((info["evals"] >= 2) & (info["evals"] <= 20))
+    # spot-check the GPU's kappa at its eps with the oracle's definition
+    for k in range(0, ns.N, 257):
+        P = ns.X[ref.idx[k]]
+        kc = ow.cond2(ow.interp_matrix(P, info["eps"][k], ow.GAUSSIAN))
+        assert abs(math.log(kc / info["kappa"][k])) < 1e-3
+    # accuracy of Delta_M Y_3^2 with the GPU-searched operator
+    u = W.sph_harm_y32(ns.X)
+    y = R.apply(op, T(u)).cpu().numpy()
+    assert np.abs(y + 12 * u).max() / np.abs(12 * u).max() < 2e-4
+
+
+@pytest.mark.parametrize("kernel", ["imq", "gaussian"])
+def test_moderate_kappa_random_field(R, kernel):
+    ns = W.icosahedral_sphere(3)
+    kid = ow.KERNELS[kernel]
+    ref = oop.build_operator(ns.X, ns.normals, 31, kid, eps=5.0)
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel=kernel, eps_override=T(ref.eps))
+    for u in (W.uniform_field(ns.N, seed=2), W.sph_harm_y32(ns.X)):
+        y = R.apply(op, T(u)).cpu().numpy()
+        assert rel_inf(y, oop.apply(ref, u)) <= 1e-8
+
+
+def test_mixed_sizes_ragged_rows(R):
+    """N = 3001 (not a multiple of 32), three stencil sizes that are not
+    multiples of 4, all rows checked."""
+    ns = W.fibonacci_sphere(3001)
+    nper = np.array([11, 17, 31])[np.arange(ns.N) % 3].astype(np.int32)
+    ref = oop.build_operator(ns.X, ns.normals, nper, ow.IMQ, eps=np.full(ns.N, 6.0))
+    op = R.build_operator(T(ns.X), T(ns.normals), T(nper, torch.int32), kernel="imq",
+                          eps_override=T(ref.eps))
+    idx, w = R.get_rows(op)
+    assert np.array_equal(idx.cpu().numpy(), ref.idx.astype(np.int32))
+    assert op.nnz == int(nper.sum())
+    u = W.uniform_field(ns.N, seed=3)
+    assert rel_inf(R.apply(op, T(u)).cpu().numpy(), oop.apply(ref, u)) <= 1e-8
+
+
+def test_stencil_equals_all_nodes_and_minimum_size(R):
+    ns = W.icosahedral_sphere(1)       # N = 42
+    for n in (2, 42):
+        ref = oop.build_operator(ns.X, ns.normals, n, ow.IMQ, eps=2.0)
+        op = R.build_operator(T(ns.X), T(ns.normals), n, kernel="imq", eps_override=T(ref.eps))
+        idx, _ = R.get_rows(op)
+        assert np.array_equal(idx.cpu().numpy(), ref.idx.astype(np.int32))
+        u = W.uniform_field(ns.N, seed=4)
+        assert rel_inf(R.apply(op, T(u)).cpu().numpy(), oop.apply(ref, u)) <= 1e-8
+
+
+def test_invalid_inputs_are_reported(R):
+    ns = W.icosahedral_sphere(1)
+    with pytest.raises(R.RbffdError) as e:
+        R.build_operator(T(ns.X), T(ns.normals), 43)
+    assert e.value.status == 1
+    X = ns.X.copy()
+    X[5, 1] = np.nan
+    with pytest.raises(R.RbffdError) as e:
+        R.build_operator(T(X), T(ns.normals), 10)
+    assert e.value.status == 1
+    # a duplicated node makes the local matrices singular (Section 2 needs
+    # distinct nodes): the search reports failure per stencil
+    X = np.vstack([ns.X, ns.X[:1]])
+    Nr = np.vstack([ns.normals, ns.normals[:1]])
+    op = R.build_operator(T(X), T(Nr), 10, allow_failures=True)
+    st = R.get_stencil_info(op)["status"].cpu().numpy()
+    assert op.status in (4, 8)
+    assert st[0] != 0 and st[42] != 0
+    assert np.sum(st == 0) >= 30
+
+
+def test_full_size_mixed_build_sampled(R):
+    """Fibonacci sphere N = 1,000,000 in four latitude bands with n = 31, 50,
+    70, 101 (the batched-build workload), searched to kappa_T = 1e12 with the
+    IMQ kernel in one launch; sampled rows checked against the oracle."""
+    ns = W.fibonacci_sphere(1_000_000)
+    nper = W.stencil_size_groups(ns.N)
+    op = R.build_operator(T(ns.X), T(ns.normals), T(nper, torch.int32), kernel="imq",
+                          kappa_target=1e12)
+    info = {k: v.cpu().numpy() for k, v in R.get_stencil_info(op).items()}
+    assert np.all(info["status"] == 0)
+    assert np.all(np.abs(np.log(info["kappa"] / 1e12)) < 0.05)
+    idx, w = R.get_rows(op)
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([rng.choice(np.where(nper == n)[0], 6, replace=False) for n in (31, 50, 70, 101)])
+    rows = np.concatenate([rows, [0, ns.N - 1]])
+    idx_r = idx[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    w_r = w[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    for r, k in enumerate(rows):
+        n = int(nper[k])
+        sref = ost.stencil(ns.X, int(k), n)
+        assert np.array_equal(idx_r[r, :n], sref.astype(np.int32))
+        wref = ow.stencil_weights(ns.X[sref], ns.normals[sref], info["eps"][k], ow.IMQ)
+        assert np.abs(w_r[r, :n] - wref).max() <= 5e-4 * np.abs(wref).max()
+        u = W.sph_harm_y32(ns.X[sref])
+        assert abs(w_r[r, :n] @ u - wref @ u) <= 1e-8 * np.abs(wref).sum() * np.abs(u).max()
+    for k in rows[::4]:
+        n = int(nper[k])
+        sref = ost.stencil(ns.X, int(k), n)
+        e_ref, _, _ = ow.search_eps(ns.X[sref], ow.IMQ, 1e12)
+        assert abs(info["eps"][k] - e_ref) <= 2e-4 + 1e-5 * e_ref
