@@ -1,0 +1,419 @@
+"""Benchmark: batched RBF-FD operator build (stencils/s at kappa_T) on one GB300.
+
+Workload (the batched-build configuration): spherical Fibonacci lattice,
+N = 1,000,000 nodes, exact normals, cut into four latitude bands of 250,000
+nodes with stencil sizes n = 31 / 50 / 70 / 101, IMQ kernel, per-stencil eps
+searched to kappa_T = 1e12 (absolute eps tolerance 1e-4) in float64, with
+the learned first guess (one network per n, trained before timing on
+plain-search eps of a sphere and a torus).  One bench step = the whole hot
+path once: stencils (kNN), learned guesses, the eps search, the weights (one
+C-ABI build_operator call), then one CUDA-graph-replayed SBDF2 + BiCGSTAB
+time step (Schnakenberg, float32) with the new operator.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launch stream, L2 flushed (256 MB write) before every step, barrier +
+synchronize around the timed region, max over ranks.  Under torchrun each
+rank builds its own copy (replicas: the build needs no exchange), so value
+= ranks x N / time ("scaling": "weak").
+
+The roofline of the dominant kernel (the eps search) counts algorithmic
+float64 flops: per stencil E_k * m^3 / 3 (m = n + 1, one symmetric
+factorisation per condition-number evaluation, E_k = the evaluations that
+launch actually performed for stencil k) over the search kernel's CUDA-event
+time, against the measured FP64 FMA peak.  The oracle's median evaluation
+counts are reported beside it.
+
+--profile runs the same pipeline once on a 40,000-node version of the
+workload (same four stencil sizes) inside an NVTX range "profiled", for ncu.
+
+--impl reference times the CPU FP64 oracle (single thread) on a bounded
+sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZES = (31, 50, 70, 101)
+N_NODES = 1_000_000
+KAPPA_T = 1e12
+METRIC = "stencils/s built at target kappa (batched mixed-n build + one IMEX step)"
+UNIT = "stencils/s"
+# DRAM bytes per launch of the search kernel from one ncu capture, keyed by
+# the hash of build.cu at the time of the capture (None when not captured).
+SEARCH_TRAFFIC = {}
+
+
+def _parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--sample", type=int, default=20, help="oracle stencils per size per step")
+    ap.add_argument("--profile", action="store_true", help="one small run for ncu (NVTX 'profiled')")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle worker (single-threaded subprocess)
+# ---------------------------------------------------------------------------
+
+def cpu_worker(per_size: int, seed: int):
+    import numpy as np
+    from oracle import operator as oop
+    from oracle import weights as ow
+    from paper_1404_0812_gb300 import workloads as W
+    ns = W.fibonacci_sphere(N_NODES)
+    nper = W.stencil_size_groups(N_NODES, SIZES)
+    rng = np.random.default_rng(seed)
+    rows = np.concatenate([rng.choice(np.where(nper == n)[0], per_size, replace=False) for n in SIZES])
+    t = time.perf_counter()
+    op = oop.build_operator(ns.X, ns.normals, nper, ow.IMQ, kappa_T=KAPPA_T, rows=rows)
+    dt = time.perf_counter() - t
+    evals = {int(n): [int(e) for e, k in zip(op.evals, rows) if nper[k] == n] for n in SIZES}
+    print(json.dumps(dict(count=len(rows), seconds=dt, evals=evals)))
+
+
+def run_cpu_sample(per_size: int, seed: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(per_size),
+                          "--sample", str(seed)], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+# clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def _file_hash(path):
+    import hashlib
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def train_networks(R, W, T, torch):
+    """One eps network per stencil size, trained on plain-search eps of a
+    Fibonacci sphere (60k) and a staggered torus (m = 100, 60k)."""
+    import numpy as np
+    nets = []
+    sets = [W.fibonacci_sphere(60_000), W.torus_staggered(100)]
+    dev = [(T(s.X), T(s.normals)) for s in sets]
+    for n in SIZES:
+        F, Y = [], []
+        for X, Nr in dev:
+            op = R.build_operator(X, Nr, n, kernel="imq", kappa_target=KAPPA_T)
+            f, y = R.features(op, X, Nr, n)
+            F.append(f)
+            Y.append(y)
+        net = R.EpsNet(n, W.mlp_pack(W.mlp_init(3 * n, seed=n)).astype(np.float32))
+        net.train(torch.cat(F).contiguous(), torch.cat(Y).contiguous(), epochs=20, batch=1024, lr=1e-3, seed=0)
+        nets.append(net)
+    return nets
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1404_0812_gb300 as R
+    from paper_1404_0812_gb300 import workloads as W
+    R._lib.load()
+    dev = torch.device("cuda", local)
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+
+    cpu = None
+    if rank == 0 and not args.profile:   # oracle sample first, before heavy GPU work
+        cpu = run_cpu_sample(args.sample, 1234)
+    n_nodes = 40_000 if args.profile else N_NODES
+
+    ns = W.fibonacci_sphere(n_nodes)
+    nper = W.stencil_size_groups(n_nodes, SIZES)
+    X, Nr, NP = T(ns.X), T(ns.normals), T(nper, torch.int32)
+    nets = None if args.no_learned else train_networks(R, W, T, torch)
+    s = W.SCHNAKENBERG
+    name, coef = R.model_coefs(s)
+    u0, v0 = W.schnakenberg_initial(n_nodes, seed=2)
+    sp = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
+                      delta_v=s["delta_v"], coef=coef, tol=1e-6, use_graph=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one_step(Xd, Nd, NPd):
+        op = R.build_operator(Xd, Nd, NPd, kernel="imq", kappa_target=KAPPA_T, mlps=nets)
+        st = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
+        R.step_imex(op, st, sp, 1)
+        return op
+
+    if args.profile:
+        for _ in range(2):
+            one_step(X, Nr, NP)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        op = one_step(X, Nr, NP)
+        uu = torch.rand(n_nodes, dtype=torch.float32, device=dev)
+        R.apply(op, uu)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_case": "fibonacci_sphere_40k_mixed_n", "N": n_nodes,
+                          "phases_ms": R.get_build_timings(op)}))
+        return
+
+    # plain search once (untimed) for the learned-vs-plain speedup
+    torch.cuda.synchronize()
+    op_plain = R.build_operator(X, Nr, NP, kernel="imq", kappa_target=KAPPA_T)
+    plain_ms = R.get_build_timings(op_plain)
+    plain_evals = R.get_stencil_info(op_plain)["evals"].double().mean().item()
+    del op_plain
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        op = one_step(X, Nr, NP)
+    torch.cuda.synchronize()
+
+    times, phases = [], []
+    l0 = R.launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            op = one_step(X, Nr, NP)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            phases.append(R.get_build_timings(op))
+            evals_t = R.get_stencil_info(op)["evals"]
+        torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    launches = R.launch_count() - l0
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = statistics.mean(times)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API from pinned host memory
+    hX = torch.from_numpy(ns.X).pin_memory()
+    hN = torch.from_numpy(ns.normals).pin_memory()
+    hP = torch.from_numpy(nper).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd = hX.to(dev, non_blocking=True)
+        Nd = hN.to(dev, non_blocking=True)
+        Pd = hP.to(dev, non_blocking=True)
+        op = one_step(Xd, Nd, Pd)
+        eps_host = R.get_stencil_info(op)["eps"].cpu()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = hX.numel() * 8 + hN.numel() * 8 + hP.numel() * 4
+    d2h = eps_host.numel() * 8
+
+    info = {k: v.cpu().numpy() for k, v in R.get_stencil_info(op).items()}
+    ok = bool(np.all((info["status"] == 0) | (info["status"] == 4)))
+
+    if rank != 0:
+        return
+    # ---- roofline of the search kernel (float64 ALU): evaluations it performed
+    E = {int(n): float(statistics.median(v)) for n, v in cpu["evals"].items()}
+    ev_np = evals_t.cpu().numpy().astype(np.float64)
+    alg_flops_search = sum(float(ev_np[nper == n].sum()) * (n + 1) ** 3 / 3.0 for n in SIZES)
+    search_ms = statistics.mean(p["search"] for p in phases)
+    peak = R.fp64_peak() / 1e3   # TFLOP/s, measured FMA throughput
+    achieved = alg_flops_search / (search_ms * 1e-3) / 1e12
+    traffic = SEARCH_TRAFFIC.get(_file_hash(os.path.join(ROOT, "paper_1404_0812_gb300", "csrc", "build.cu")))
+    # apply bandwidth of the built operator (HBM; matrix far larger than L2)
+    apply = {}
+    for dt, code in ((torch.float32, R.F32), (torch.float64, R.F64)):
+        uu = torch.rand(N_NODES, dtype=dt, device=dev)
+        yy = torch.empty_like(uu)
+        for _ in range(3):
+            R.apply(op, uu, yy)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for _ in range(20):
+            R.apply(op, uu, yy)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ams = a0.elapsed_time(a1) / 20
+        gbs = op.apply_bytes(code) / (ams * 1e-3) / 1e9
+        apply["f32" if code == R.F32 else "f64"] = {"ms": round(ams, 4), "GB_s": round(gbs, 1)}
+    hbm = None
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        hbm = 6800.0
+    for v in apply.values():
+        v["frac_of_measured_hbm"] = round(v["GB_s"] / hbm, 3)
+    learned_ms = statistics.mean(p["guess"] + p["search"] for p in phases)
+    value = ws * N_NODES / (ms * 1e-3)
+    cpu_value = cpu["count"] / cpu["seconds"]
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fibonacci_sphere_1M_mixed_n", "N": N_NODES, "n": list(SIZES),
+                   "groups": "4 contiguous index bands of 250k", "kernel": "imq", "kappa_T": KAPPA_T,
+                   "eps_tol": 1e-4, "learned_start": nets is not None,
+                   "imex_step": "schnakenberg f32, 1 step, CUDA graph", "l2": "flushed (256 MB write) per step",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "kernel": "search_kernel (float64)", "achieved": round(achieved, 4),
+                     "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "peak_source": "measured FP64 FMA microbenchmark (rbffd_fp64_peak)",
+                     "traffic": traffic, "flops_per_launch": alg_flops_search,
+                     "evals_mean_by_n": {int(n): round(float(ev_np[nper == n].mean()), 3) for n in SIZES},
+                     "E_oracle_median": E, "search_ms": round(search_ms, 3)},
+        "phases_ms": {k: round(statistics.mean(p[k] for p in phases), 3) for k in phases[0]},
+        "learned_speedup": {"plain_search_ms": round(plain_ms["search"], 3),
+                            "learned_guess_plus_search_ms": round(learned_ms, 3),
+                            "speedup": round(plain_ms["search"] / learned_ms, 3),
+                            "plain_evals_mean": round(plain_evals, 3),
+                            "learned_evals_mean": round(float(info["evals"].mean()), 3),
+                            "accepted_fraction": round(float((info["status"] == 4).mean()), 4)},
+        "apply": apply,
+        "all_stencils_ok": ok,
+        "e2e": {"value": round(N_NODES / statistics.mean(e2e_times), 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": {"value": round(cpu_value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu['count']} stencils ({args.sample} per n) of the same 1M-node "
+                                   f"workload: brute-force stencil, Brent eps search, full G^d weights"},
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    times, counts, evals = [], [], []
+    for i in range(args.warmup + args.steps):
+        r = run_cpu_sample(args.sample, 1000 + i)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+            counts.append(r["count"])
+    value = sum(counts) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "fibonacci_sphere_1M_mixed_n", "N": N_NODES, "n": list(SIZES),
+                   "kernel": "imq", "kappa_T": KAPPA_T, "eps_tol": 1e-4},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.sample} stencils per n per step of the 1M-node workload"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = _parse()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker, args.sample)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

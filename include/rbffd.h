@@ -79,6 +79,24 @@ typedef struct {
 void rbffd_build_opts_default(rbffd_build_opts* opts);
 
 /*
+ * rbffd_autotune_build - choose the launch shape (threads per block, resident
+ * blocks per SM) of the build's lane-per-stencil kernels for this device and
+ * workload (a systems addition; the paper has no GPU).  Builds the operator
+ * on every (N / sample)-th node (same surface and stencil sizes, coarser
+ * spacing) with each candidate shape, times the search + weights phases with
+ * CUDA events, and returns the fastest in *block_threads / *blocks_per_sm
+ * (and its time in *best_ms, -1 when it came from the cache).  Arguments as
+ * in rbffd_build_operator; cache_path (may be NULL) is a text file of
+ * previous results keyed by device, stencil sizes, kernel and kappa_T; a hit
+ * skips the timing.  Synchronises the stream.
+ */
+rbffd_status rbffd_autotune_build(const double* nodes, const double* normals, int64_t N,
+                                  const int32_t* n_per_node, int n_uniform,
+                                  const rbffd_build_opts* opts, int64_t sample,
+                                  const char* cache_path, void* stream, int* block_threads,
+                                  int* blocks_per_sm, double* best_ms);
+
+/*
  * rbffd_build_operator - the discrete surface Laplacian L_X (Section 4).
  *
  * For every node k: its stencil P_k (k first, then its n_k - 1 nearest other
@@ -188,6 +206,15 @@ rbffd_status rbffd_get_stencil_info(const rbffd_op* op, double* eps, double* kap
  * hold the row's own node and weight 0).  n_max = rbffd_op_max_n(op).
  */
 rbffd_status rbffd_get_rows(const rbffd_op* op, int32_t* idx, double* w, void* stream);
+/*
+ * Device time of the phases of the last rbffd_build_operator that produced
+ * op, from CUDA events recorded on its stream around the launches (ms):
+ * [0] stencils (kNN), [1] learned first guess, [2] shape-parameter search,
+ * [3] weights.  Host-side work between launches is not included.
+ */
+rbffd_status rbffd_get_build_timings(const rbffd_op* op, double ms[4]);
+/* Kernel launches issued by this library since it was loaded. */
+int64_t rbffd_launch_count(void);
 int64_t rbffd_op_nodes(const rbffd_op* op);
 int rbffd_op_max_n(const rbffd_op* op);
 int64_t rbffd_op_nnz(const rbffd_op* op);      /* sum of n_k (Section 4.1) */
@@ -248,6 +275,15 @@ rbffd_status rbffd_mlp_train(rbffd_mlp* mlp, const float* feats, const float* ta
 /* Predictions ln(eps * r_s) for count feature rows (device in / out). */
 rbffd_status rbffd_mlp_predict(const rbffd_mlp* mlp, const float* feats, int64_t count,
                                float* out, void* stream);
+
+/*
+ * Failure-detection self test of the bounded grid barrier used by
+ * rbffd_step_imex: launches one block that waits at the barrier for a second
+ * arrival that never comes.  The wait gives up after about a second, the
+ * kernel returns, and the call returns RBFFD_TIMEOUT with the CUDA context
+ * still usable (any other status means the bound is broken).
+ */
+rbffd_status rbffd_selftest_barrier_timeout(void* stream);
 
 /* ------------------------------------------------------------------------ */
 const char* rbffd_status_str(rbffd_status s);

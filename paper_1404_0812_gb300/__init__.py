@@ -102,6 +102,29 @@ def build_operator(nodes, normals, n=31, kernel="imq", kappa_target=1e12, eps_to
     return op
 
 
+def autotune_build(nodes, normals, n=31, kernel="imq", kappa_target=1e12, sample=50_000,
+                   cache_path=None, stream=None):
+    """rbffd_autotune_build -> dict(block_threads, blocks_per_sm, ms)."""
+    lib = _lib.load()
+    nodes = _dev(nodes, torch.float64)
+    normals = _dev(normals, torch.float64)
+    o = _lib.BuildOpts()
+    lib.rbffd_build_opts_default(C.byref(o))
+    o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    o.kappa_target = float(kappa_target)
+    if isinstance(n, torch.Tensor):
+        nptr, nu = C.c_void_p(_dev(n, torch.int32).data_ptr()), 0
+    else:
+        nptr, nu = None, int(n)
+    t, b, ms = C.c_int(), C.c_int(), C.c_double()
+    path = None if cache_path is None else str(cache_path).encode()
+    _lib.check(lib.rbffd_autotune_build(C.c_void_p(nodes.data_ptr()), C.c_void_p(normals.data_ptr()),
+                                        nodes.shape[0], nptr, nu, C.byref(o), int(sample), path,
+                                        _stream(stream), C.byref(t), C.byref(b), C.byref(ms)),
+               "rbffd_autotune_build")
+    return dict(block_threads=t.value, blocks_per_sm=b.value, ms=ms.value)
+
+
 def apply(op: Operator, u, y=None, stream=None):
     """rbffd_apply: y = L_X u (float32 or float64 by u's dtype)."""
     lib = _lib.load()
@@ -135,6 +158,18 @@ def get_rows(op: Operator, stream=None):
     w = torch.empty((op.N, nm), dtype=torch.float64, device="cuda")
     _lib.check(lib.rbffd_get_rows(op.handle, _ptr(idx), _ptr(w), _stream(stream)), "rbffd_get_rows")
     return idx, w
+
+
+def get_build_timings(op: Operator) -> dict:
+    """rbffd_get_build_timings -> device ms of knn / guess / search / weights."""
+    arr = (C.c_double * 4)()
+    _lib.check(_lib.load().rbffd_get_build_timings(op.handle, arr), "rbffd_get_build_timings")
+    return dict(knn=arr[0], guess=arr[1], search=arr[2], weights=arr[3])
+
+
+def launch_count() -> int:
+    """rbffd_launch_count: kernel launches issued by the library so far."""
+    return int(_lib.load().rbffd_launch_count())
 
 
 def destroy(op: Operator):
@@ -220,3 +255,93 @@ def fp64_peak(stream=None) -> float:
     g = C.c_double()
     _lib.check(_lib.load().rbffd_fp64_peak(_stream(stream), C.byref(g)), "rbffd_fp64_peak")
     return g.value
+
+
+def selftest_barrier_timeout(stream=None) -> int:
+    """rbffd_selftest_barrier_timeout; returns the status (TIMEOUT expected)."""
+    return int(_lib.load().rbffd_selftest_barrier_timeout(_stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# learned eps warm start
+# ---------------------------------------------------------------------------
+
+class EpsNet:
+    """Handle of a library-owned eps network (rbffd_mlp) for stencil size n."""
+
+    def __init__(self, n: int, params=None):
+        import numpy as np
+        lib = _lib.load()
+        self.n = int(n)
+        self.P = int(lib.rbffd_mlp_param_count(self.n))
+        h = C.c_void_p()
+        buf = None
+        if params is not None:
+            buf = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+            if buf.size != self.P:
+                raise ValueError(f"expected {self.P} parameters, got {buf.size}")
+        _lib.check(lib.rbffd_mlp_create(self.n, None if buf is None else buf.ctypes.data_as(C.c_void_p),
+                                        C.byref(h)), "rbffd_mlp_create")
+        self.handle = h
+
+    def params(self):
+        import numpy as np
+        out = np.empty(self.P, dtype=np.float32)
+        _lib.check(_lib.load().rbffd_mlp_get_params(self.handle, out.ctypes.data_as(C.c_void_p)),
+                   "rbffd_mlp_get_params")
+        return out
+
+    def loss_grad(self, feats, target, stream=None):
+        """rbffd_mlp_loss_grad -> (grad CUDA float32 tensor, loss float)."""
+        feats = _dev(feats, torch.float32)
+        target = _dev(target, torch.float32)
+        g = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        l = torch.empty(1, dtype=torch.float32, device="cuda")
+        _lib.check(_lib.load().rbffd_mlp_loss_grad(self.handle, _ptr(feats), _ptr(target),
+                                                   target.shape[0], _ptr(g), _ptr(l), _stream(stream)),
+                   "rbffd_mlp_loss_grad")
+        return g, float(l.item())
+
+    def train(self, feats, target, epochs=20, batch=1024, lr=1e-3, seed=0, stream=None):
+        """rbffd_mlp_train -> list of per-epoch mean losses."""
+        import numpy as np
+        feats = _dev(feats, torch.float32)
+        target = _dev(target, torch.float32)
+        losses = np.zeros(epochs, dtype=np.float32)
+        _lib.check(_lib.load().rbffd_mlp_train(self.handle, _ptr(feats), _ptr(target), target.shape[0],
+                                               int(epochs), int(batch), float(lr), int(seed),
+                                               _stream(stream), losses.ctypes.data_as(C.c_void_p)),
+                   "rbffd_mlp_train")
+        return losses.tolist()
+
+    def predict(self, feats, stream=None):
+        feats = _dev(feats, torch.float32)
+        count = feats.shape[0]
+        out = torch.empty(count, dtype=torch.float32, device="cuda")
+        _lib.check(_lib.load().rbffd_mlp_predict(self.handle, _ptr(feats), count, _ptr(out),
+                                                 _stream(stream)), "rbffd_mlp_predict")
+        return out
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.load().rbffd_mlp_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def features(op: Operator, nodes, normals, n: int, with_target=True, stream=None):
+    """rbffd_features -> (feats count x 3n, target or None) for the rows of
+    stencil size n, in node order."""
+    lib = _lib.load()
+    cnt = C.c_int64()
+    # count = number of rows with this stencil size; ask first with a probe size
+    N = op.N
+    feats = torch.empty((N, 3 * n), dtype=torch.float32, device="cuda")
+    target = torch.empty(N, dtype=torch.float32, device="cuda") if with_target else None
+    _lib.check(lib.rbffd_features(op.handle, _ptr(_dev(nodes, torch.float64)),
+                                  _ptr(_dev(normals, torch.float64)), int(n), _ptr(feats), _ptr(target),
+                                  C.byref(cnt), _stream(stream)), "rbffd_features")
+    c = int(cnt.value)
+    return feats[:c], (target[:c] if with_target else None)

@@ -53,10 +53,15 @@ SIGNATURES = {
     "rbffd_build_operator": (C.c_int, [vp, vp, C.c_int64, vp, C.c_int, C.POINTER(BuildOpts), vp,
                                        C.POINTER(vp)]),
     "rbffd_apply": (C.c_int, [vp, vp, vp, C.c_int, vp]),
+    "rbffd_autotune_build": (C.c_int, [vp, vp, C.c_int64, vp, C.c_int, C.POINTER(BuildOpts), C.c_int64,
+                                       C.c_char_p, vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_double)]),
     "rbffd_step_imex": (C.c_int, [vp, C.POINTER(State), C.POINTER(StepParams), C.c_int64, vp,
                                   C.POINTER(StepReport)]),
     "rbffd_get_stencil_info": (C.c_int, [vp, vp, vp, vp, vp, vp]),
     "rbffd_get_rows": (C.c_int, [vp, vp, vp, vp]),
+    "rbffd_get_build_timings": (C.c_int, [vp, C.POINTER(C.c_double)]),
+    "rbffd_launch_count": (C.c_int64, []),
     "rbffd_op_nodes": (C.c_int64, [vp]),
     "rbffd_op_max_n": (C.c_int, [vp]),
     "rbffd_op_nnz": (C.c_int64, [vp]),
@@ -71,6 +76,7 @@ SIGNATURES = {
     "rbffd_mlp_train": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_uint64,
                                   vp, vp]),
     "rbffd_mlp_predict": (C.c_int, [vp, vp, C.c_int64, vp, vp]),
+    "rbffd_selftest_barrier_timeout": (C.c_int, [vp]),
     "rbffd_status_str": (C.c_char_p, [C.c_int]),
     "rbffd_last_error": (C.c_char_p, []),
     "rbffd_fp64_peak": (C.c_int, [vp, C.POINTER(C.c_double)]),

@@ -4,6 +4,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <map>
@@ -19,6 +20,9 @@ void set_error(const char* fmt, ...) {
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
 }
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add(k); }
 
 int sm_count() {
     int dev = 0, n = 0;
@@ -130,6 +134,7 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
                                   const rbffd_build_opts* opts_in, void* stream, rbffd_op** out) {
     RBFFD_CHECK_ARG(out != nullptr, "out is NULL");
     *out = nullptr;
+    (void)cudaGetLastError();   // an earlier failure elsewhere is not ours
     RBFFD_CHECK_ARG(nodes != nullptr && normals != nullptr, "nodes / normals are NULL");
     RBFFD_CHECK_ARG(N >= 2 && N < (int64_t)1 << 31, "N must be in [2, 2^31)");
     rbffd_build_opts o;
@@ -219,15 +224,27 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
         TRY_OP(cudaStreamSynchronize(st));
     } else {
         iota_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->row_node, N);
+        note_launch();
         TRY_OP(cudaGetLastError());
     }
     init_info<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->eps, op->kappa, op->evals, op->status,
                                                            o.eps_override, N);
+    note_launch();
     TRY_OP(cudaGetLastError());
 
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i) TRY_OP(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
+        }
+    } evguard{ev};
+    TRY_OP(cudaEventRecord(ev[0], st));
     // ---- stencils
     rbffd_status s = knn_stencils(op, nodes, normals, st);
     if (s != RBFFD_OK) return fail(s);
+    TRY_OP(cudaEventRecord(ev[1], st));
 
     // ---- shape parameters
     rbffd_status search_status = RBFFD_OK;
@@ -241,13 +258,16 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
                 return fail(s);
             }
         }
+        TRY_OP(cudaEventRecord(ev[2], st));
         s = build_search(op, nodes, normals, o, guess, st);
+        TRY_OP(cudaEventRecord(ev[3], st));
         if (guess) cudaFreeAsync(guess, st);
         if (s != RBFFD_OK) return fail(s);
         int* bad = nullptr;
         TRY_OP(cudaMallocAsync(&bad, sizeof(int), st));
         TRY_OP(cudaMemsetAsync(bad, 0, sizeof(int), st));
         count_status<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->status, N, bad);
+        note_launch();
         int hb = 0;
         TRY_OP(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
         TRY_OP(cudaStreamSynchronize(st));
@@ -257,10 +277,20 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
             search_status = RBFFD_EPS_SEARCH_FAILED;
         }
     }
+    else {
+        TRY_OP(cudaEventRecord(ev[2], st));
+        TRY_OP(cudaEventRecord(ev[3], st));
+    }
     // ---- weights
     s = build_weights(op, nodes, normals, o, op->eps, st);
     if (s != RBFFD_OK && s != RBFFD_ESINGULAR) return fail(s);
+    TRY_OP(cudaEventRecord(ev[4], st));
     TRY_OP(cudaStreamSynchronize(st));
+    for (int i = 0; i < 4; ++i) {
+        float ms = 0.f;
+        TRY_OP(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+        op->phase_ms[i] = ms;
+    }
     *out = op;
     if (search_status != RBFFD_OK) return search_status;
     return s;
@@ -271,7 +301,7 @@ rbffd_status rbffd_apply(const rbffd_op* op, const void* u, void* y, int dtype, 
     RBFFD_CHECK_ARG(op && u && y, "NULL argument");
     RBFFD_CHECK_ARG(dtype == RBFFD_F32 || dtype == RBFFD_F64, "dtype");
     RBFFD_CHECK_ARG(u != y, "u and y alias");
-    return apply_launch(op, u, y, dtype, as_stream(stream));
+    return apply_launch(op, u, y, dtype, as_stream(stream));   // counts its launch
 }
 
 rbffd_status rbffd_get_stencil_info(const rbffd_op* op, double* eps, double* kappa, int32_t* evals,
@@ -290,10 +320,17 @@ rbffd_status rbffd_get_rows(const rbffd_op* op, int32_t* idx, double* w, void* s
     cudaStream_t st = as_stream(stream);
     rows_kernel<<<(unsigned)((op->N + 127) / 128), 128, 0, st>>>(op->idx, op->w64, op->row_node, op->gi,
                                                                  op->n_max, op->N, idx, w);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     return RBFFD_OK;
 }
 
+rbffd_status rbffd_get_build_timings(const rbffd_op* op, double ms[4]) {
+    RBFFD_CHECK_ARG(op && ms, "NULL argument");
+    for (int i = 0; i < 4; ++i) ms[i] = op->phase_ms[i];
+    return RBFFD_OK;
+}
+int64_t rbffd_launch_count(void) { return g_launches.load(); }
 int64_t rbffd_op_nodes(const rbffd_op* op) { return op ? op->N : 0; }
 int rbffd_op_max_n(const rbffd_op* op) { return op ? op->n_max : 0; }
 int64_t rbffd_op_nnz(const rbffd_op* op) { return op ? op->nnz : 0; }

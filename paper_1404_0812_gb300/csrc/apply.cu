@@ -64,6 +64,7 @@ rbffd_status apply_launch(const rbffd_op* op, const void* u, void* y, int dtype,
     else
         apply_kernel<double><<<blocks, 256, 0, st>>>(op->idx, op->w64, op->row_node, op->gi,
                                                       (const double*)u, (double*)y, R);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     return RBFFD_OK;
 }

@@ -45,7 +45,9 @@ namespace rbffd {
 namespace {
 
 constexpr int LANCZOS_KMAX = 24;
-constexpr double LANCZOS_RTOL = 1e-6;
+constexpr double LANCZOS_RTOL = 1e-6;       // relative change that stops a Lanczos run
+constexpr int LANCZOS_KMIN = 3;             // never stop before this many steps
+constexpr double ACCEPT_MARGIN = 1e-4;      // shrink the accept band by this
 constexpr double F_FAIL = 60.0;         // F value used when Phi is not numerically SPD
 constexpr int BRACKET_MAX = 40;
 
@@ -66,24 +68,29 @@ struct Layout {
     int size;    // doubles per lane
 };
 
-__host__ __device__ inline Layout make_layout(int m) {
+// full = true: the weights kernel's layout (adds the Phi copy, normals and
+// the gradient vectors); the search needs only r^2, L and the vectors.
+__host__ __device__ inline Layout make_layout(int m, bool full) {
     Layout l;
     l.m = m;
     l.P = m * (m + 1) / 2;
     int o = 0;
     l.R2 = o; o += l.P;
     l.L = o; o += l.P;
-    l.PH = o; o += l.P;
     l.XS = o; o += 3 * m;
-    l.NS = o; o += 3 * m;
     l.U = o; o += m;
     l.ID = o; o += m;
     l.Q0 = o; o += m;
     l.Q1 = o; o += m;
     l.Q2 = o; o += m;
     l.T0 = o; o += m;
-    l.GV = o; o += 3 * m;
-    l.HV = o; o += 3 * m;
+    l.PH = l.NS = l.GV = l.HV = -1;
+    if (full) {
+        l.PH = o; o += l.P;
+        l.NS = o; o += 3 * m;
+        l.GV = o; o += 3 * m;
+        l.HV = o; o += 3 * m;
+    }
     l.size = o;
     return l;
 }
@@ -350,20 +357,25 @@ __device__ double tri_max_abs(const float* a, const float* b2, int k, double sca
 // Lanczos with op = A^{-1} (inv = true) or A (inv = false) on augmented
 // vectors (m entries in a region + one border scalar).  Returns the extreme
 // |Ritz value|.  Requires L, ID, U (Phi^{-1} 1) and s.
-__device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool inv, double s) {
+__device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool inv, double s,
+                                  double rtol) {
     const int m = ly.m;
     float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
     double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX];
     int qp = ly.Q0, q = ly.Q1, w = ly.Q2;
-    // start vector: cos(1.7 i + 0.3) + 0.1 on the n nodes and the border
+    // start vector.  For A^{-1}: cos(1.7 i + 0.3) + 0.1 on the n nodes and the
+    // border (no preferred direction).  For A: mostly the constant vector,
+    // close to the dominant eigenvector when Phi is nearly flat (Phi ~ 1 1^T),
+    // plus the same oscillation at 1% so no eigenvector is missed.
     double nrm2 = 0.0;
     for (int i = 0; i < m; ++i) {
-        double v = i < n ? cos(1.7 * i + 0.3) + 0.1 : 0.0;
+        double osc = cos(1.7 * i + 0.3) + 0.1;
+        double v = i < n ? (inv ? osc : 1.0 + 0.01 * osc) : 0.0;
         S[q + i] = v;
         S[qp + i] = 0.0;
         nrm2 += v * v;
     }
-    double qb = cos(1.7 * n + 0.3) + 0.1, qpb = 0.0;
+    double qb = inv ? cos(1.7 * n + 0.3) + 0.1 : 0.1, qpb = 0.0;
     nrm2 += qb * qb;
     double inrm = rsqrt(nrm2);
     for (int i = 0; i < n; ++i) S[q + i] *= inrm;
@@ -420,7 +432,7 @@ __device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool i
             b2[i] = bb * bb;
         }
         ext = tri_max_abs(al, b2, j + 1, G);
-        if (j >= 1 && fabs(ext - prev) <= LANCZOS_RTOL * ext) break;
+        if (j + 1 >= LANCZOS_KMIN && fabs(ext - prev) <= rtol * ext) break;
         if (bn <= 1e-14 * fabs(a)) break;
         prev = ext;
         beta = bn;
@@ -437,7 +449,8 @@ __device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool i
 }
 
 // kappa_2(A(eps_s)); +inf when Phi is not numerically positive definite.
-__device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel, double eps_s) {
+__device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel, double eps_s,
+                             double rtol) {
     assemble_phi(S, ly, n, kernel, eps_s, ly.L, -1);
     if (!cholesky(S, ly)) return INFINITY;
     for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
@@ -445,8 +458,8 @@ __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel,
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += S[ly.U + i];
     if (!(s > 0.0)) return INFINITY;
-    double tinv = lanczos_extreme(S, ly, n, true, s);
-    double lmax = lanczos_extreme(S, ly, n, false, s);
+    double tinv = lanczos_extreme(S, ly, n, true, s, rtol);
+    double lmax = lanczos_extreme(S, ly, n, false, s, rtol);
     double k = lmax * tinv;
     return isfinite(k) ? k : INFINITY;
 }
@@ -528,20 +541,25 @@ __device__ void enter_brent(Search& s, double xl, double fl, double kl, double x
     s.phase = PH_BRENT;
 }
 
+// dF/dx near the root, F = ln(kappa / kappa_T), x = ln(eps r_s): about
+// -(11 + n / 10) for both kernels on quasi-uniform surface stencils
+// (measured); only used to aim the first secant step.
+__device__ inline double slope_model(int n) { return -(11.0 + 0.1 * n); }
+
 // Consume F(x_next) = f (kappa k).  Sets phase PH_DONE when finished.
 __device__ void search_update(Search& s, double f, double k, double tol_s, int max_evals,
-                              double acc_lo, double acc_hi, bool learned) {
+                              double acc_lo, double acc_hi, bool learned, int n) {
     s.evals++;
     double x = s.x_next;
     if (s.phase == PH_FIRST) {
-        if (learned && k >= acc_lo && k <= acc_hi) {
+        if (learned && k >= acc_lo * (1.0 + ACCEPT_MARGIN) && k <= acc_hi * (1.0 - ACCEPT_MARGIN)) {
             s.b = x; s.fb = f; s.kb = k;
             s.status = RBFFD_STENCIL_ACCEPTED_PREDICTION;
             s.phase = PH_DONE;
             return;
         }
         s.x0 = x; s.f0 = f; s.k0 = k;
-        s.x_next = x + clampd(f / 8.0, -3.0, 3.0);
+        s.x_next = x + clampd(-f / slope_model(n), -3.0, 3.0);
         if (f == 0.0) {
             s.b = x; s.kb = k; s.phase = PH_DONE;
             return;
@@ -567,7 +585,7 @@ __device__ void search_update(Search& s, double f, double k, double tol_s, int m
             return;
         }
         double slope = (f - s.f0) / (x - s.x0);
-        if (!(slope < -0.5) || !isfinite(slope)) slope = -8.0;
+        if (!(slope < -0.5) || !isfinite(slope)) slope = slope_model(n);
         double step = clampd(-f / slope, -3.0, 3.0);
         double dir = f > 0.0 ? 1.0 : -1.0;   // F decreases with x
         if (step * dir < 0.05) step = 0.05 * dir;
@@ -613,7 +631,7 @@ __global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
     const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     Lane S{A.scratch + warp_global * 32 * (int64_t)A.lane_size + lane_id};
     int g = 0;
-    Layout ly = make_layout(A.gi.npad[0]);
+    Layout ly = make_layout(A.gi.npad[0], false);
     bool have = false;
     int64_t lr = 0, r = 0;
     int n = A.gi.n[0];
@@ -643,14 +661,14 @@ __global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
         }
         if (__ballot_sync(0xffffffffu, have) == 0) {
             if (++g >= A.gi.ngroups) break;
-            ly = make_layout(A.gi.npad[g]);
+            ly = make_layout(A.gi.npad[g], false);
             n = A.gi.n[g];
             continue;
         }
         if (have) {
-            double k = eval_kappa(S, ly, n, A.kernel, exp(st.x_next));
+            double k = eval_kappa(S, ly, n, A.kernel, exp(st.x_next), LANCZOS_RTOL);
             search_update(st, F_of(k, A.kT), k, tol_s, A.max_evals, A.acc_lo * A.kT, A.acc_hi * A.kT,
-                          learned);
+                          learned, n);
             if (st.phase == PH_DONE) {
                 int node = A.row_node[r];
                 A.eps[node] = exp(st.b) / geo.rs;
@@ -701,7 +719,7 @@ __global__ void __launch_bounds__(128) weights_kernel(WeightArgs A) {
         const int g = group_of_row(A.gi, r);
         const int n = A.gi.n[g], npad = A.gi.npad[g];
         const int64_t lr = r - A.gi.row_begin[g], off = A.gi.ell_off[g];
-        const Layout ly = make_layout(npad);
+        const Layout ly = make_layout(npad, true);
         Geo geo = load_geometry(S, ly, n, A.idx, off, npad, lr, A.X, A.NR, true);
         int node = A.row_node[r];
         double eps_s = A.eps_node[node] * geo.rs;
@@ -798,7 +816,7 @@ rbffd_status build_search(rbffd_op* op, const double* nodes, const double* norma
     const GroupInfo& gi = op->gi;
     int mmax = 0;
     for (int g = 0; g < gi.ngroups; ++g) mmax = std::max(mmax, gi.npad[g]);
-    Layout ly = make_layout(mmax);
+    Layout ly = make_layout(mmax, false);
     LaunchShape ls = launch_shape(o, op->N);
     RBFFD_CHECK_ARG(ls.threads % 32 == 0 && ls.threads <= 128, "block_threads must be 32..128, x32");
     int64_t lanes = (int64_t)ls.blocks * ls.threads;
@@ -827,6 +845,7 @@ rbffd_status build_search(rbffd_op* op, const double* nodes, const double* norma
     A.evals = op->evals;
     A.status = op->status;
     search_kernel<<<ls.blocks, ls.threads, 0, st>>>(A);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     RBFFD_CUDA_TRY(cudaFreeAsync(scratch, st));
     RBFFD_CUDA_TRY(cudaFreeAsync(ctr, st));
@@ -838,7 +857,7 @@ rbffd_status build_weights(rbffd_op* op, const double* nodes, const double* norm
     const GroupInfo& gi = op->gi;
     int mmax = 0;
     for (int g = 0; g < gi.ngroups; ++g) mmax = std::max(mmax, gi.npad[g]);
-    Layout ly = make_layout(mmax);
+    Layout ly = make_layout(mmax, true);
     LaunchShape ls = launch_shape(o, op->N);
     RBFFD_CHECK_ARG(ls.threads % 32 == 0 && ls.threads <= 128, "block_threads must be 32..128, x32");
     int64_t lanes = (int64_t)ls.blocks * ls.threads;
@@ -862,6 +881,7 @@ rbffd_status build_weights(rbffd_op* op, const double* nodes, const double* norm
     A.status = op->status;
     A.nfail = nfail;
     weights_kernel<<<ls.blocks, ls.threads, 0, st>>>(A);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     int hf = 0;
     RBFFD_CUDA_TRY(cudaMemcpyAsync(&hf, nfail, sizeof(int), cudaMemcpyDeviceToHost, st));

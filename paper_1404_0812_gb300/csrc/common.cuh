@@ -20,6 +20,7 @@ void set_error(const char* fmt, ...);
     do {                                                                          \
         cudaError_t _e = (expr);                                                  \
         if (_e != cudaSuccess) {                                                  \
+            (void)cudaGetLastError(); /* do not leave it for the next call */    \
             ::rbffd::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,         \
                                cudaGetErrorString(_e));                           \
             return _e == cudaErrorMemoryAllocation ? RBFFD_ENOMEM : RBFFD_ECUDA;  \
@@ -35,6 +36,9 @@ void set_error(const char* fmt, ...);
     } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// count of kernel launches issued by the library (reported to callers)
+void note_launch(int k = 1);
 
 // ---------------------------------------------------------------------------
 // sliced ELL layout.  Rows are grouped by stencil size; within a group rows
@@ -90,6 +94,7 @@ struct rbffd_op {
     int32_t* evals;             // N
     int32_t* status;            // N
     rbffd_step_ws* step;        // lazily created stepping workspace
+    double phase_ms[4];         // device time of build phases (events)
 };
 
 struct rbffd_mlp {

@@ -117,11 +117,13 @@ rbffd_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStre
     RBFFD_CUDA_TRY(cudaMallocAsync(&bs, nb * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMallocAsync(&bo, nb * sizeof(int32_t), st));
     scan_block<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, bs);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     if (nb > 1) {
         rbffd_status r = exclusive_scan(bs, bo, nb, st);
         if (r != RBFFD_OK) return r;
         scan_add<<<(unsigned)nb, SCAN_T, 0, st>>>(out, n, bo);
+        note_launch();
         RBFFD_CUDA_TRY(cudaGetLastError());
     }
     RBFFD_CUDA_TRY(cudaFreeAsync(bs, st));
@@ -251,7 +253,9 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     RBFFD_CUDA_TRY(cudaMallocAsync(&bb_d, 7 * sizeof(double), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(bb_d + 6, 0, sizeof(int), st));
     bbox_partial<<<nb, BB_THREADS, 0, st>>>(nodes, normals, N, part, reinterpret_cast<int*>(bb_d + 6));
+    note_launch();
     bbox_final<<<1, 32, 0, st>>>(part, nb, bb_d);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     double bb[7];
     RBFFD_CUDA_TRY(cudaMemcpyAsync(bb, bb_d, sizeof(bb), cudaMemcpyDeviceToHost, st));
@@ -305,13 +309,16 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     RBFFD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     unsigned nbN = (unsigned)((N + 255) / 256);
     cell_of_nodes<<<nbN, 256, 0, st>>>(nodes, N, g, cell, count);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     rbffd_status rs = exclusive_scan(count, start, total + 1, st);
     if (rs != RBFFD_OK) return rs;
     scatter_nodes<<<nbN, 256, 0, st>>>(nodes, N, cell, start, cursor, sidx, sx);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     knn_query<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(nodes, op->row_node, N, op->gi, g, start,
                                                             sidx, sx, op->idx, err);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     int herr = 0;
     RBFFD_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -337,6 +337,7 @@ rbffd_status predict_launch(const rbffd_mlp* m, const float* feats, int64_t coun
     unsigned tiles = (unsigned)((count + TS - 1) / TS);
     mlp_tile<<<tiles, NT, tile_smem(m->D), st>>>(m->params, m->D, feats, nullptr, nullptr, count, 0.f,
                                                  0, out, nullptr, nullptr);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     return RBFFD_OK;
 }
@@ -357,6 +358,7 @@ __global__ void fill_nan(float* a, int64_t n) {
 rbffd_status mlp_guess(const rbffd_op* op, const double* nodes, const double* normals,
                        const rbffd_build_opts& o, float* guess_rows, cudaStream_t st) {
     fill_nan<<<(unsigned)((op->N + 255) / 256), 256, 0, st>>>(guess_rows, op->N);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     for (int g = 0; g < op->gi.ngroups; ++g) {
         const rbffd_mlp* net = nullptr;
@@ -369,11 +371,13 @@ rbffd_status mlp_guess(const rbffd_op* op, const double* nodes, const double* no
         RBFFD_CUDA_TRY(cudaMallocAsync(&pred, count * sizeof(float), st));
         features_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
             nodes, normals, op->idx, op->row_node, op->gi, g, nullptr, feats, nullptr);
+        note_launch();
         RBFFD_CUDA_TRY(cudaGetLastError());
         rbffd_status s = predict_launch(net, feats, count, pred, st);
         if (s != RBFFD_OK) return s;
         scatter_guess<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(pred, count, op->gi.row_begin[g],
                                                                        guess_rows);
+        note_launch();
         RBFFD_CUDA_TRY(cudaGetLastError());
         cudaFreeAsync(feats, st);
         cudaFreeAsync(pred, st);
@@ -441,6 +445,7 @@ rbffd_status rbffd_features(const rbffd_op* op, const double* nodes, const doubl
     if (count_host) *count_host = count;
     features_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(nodes, normals, op->idx, op->row_node,
                                                                      op->gi, g, op->eps, feats, target);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     return RBFFD_OK;
 }
@@ -458,10 +463,12 @@ rbffd_status rbffd_mlp_loss_grad(const rbffd_mlp* mc, const float* feats, const 
     mlp_tile<<<(unsigned)tiles, NT, tile_smem(m->D), st>>>(m->params, m->D, feats, target, nullptr, count,
                                                            1.f / (float)count, 1, nullptr, m->partial,
                                                            m->loss + 4096);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     reduce_grad<<<(unsigned)((m->P + 255) / 256), 256, 0, st>>>(m->partial, (int)tiles, m->P, m->loss + 4096,
                                                                 grad, m->loss, nullptr, nullptr, nullptr, 0,
                                                                 0.f, 0);
+    note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     if (loss) {
         // mean squared error = sum of squares / count
@@ -508,9 +515,11 @@ rbffd_status rbffd_mlp_train(rbffd_mlp* m, const float* feats, const float* targ
             mlp_tile<<<tiles, NT, tile_smem(m->D), st>>>(m->params, m->D, feats, target, perm_d + b0, nb,
                                                          1.f / (float)nb, 1, nullptr, m->partial,
                                                          m->loss + 4096);
+            note_launch();
             reduce_grad<<<(unsigned)((m->P + 255) / 256), 256, 0, st>>>(
                 m->partial, (int)tiles, m->P, m->loss + 4096, nullptr, m->loss, m->params, m->adam_m,
                 m->adam_v, m->adam_t, lr, (int)b);
+            note_launch();
         }
         RBFFD_CUDA_TRY(cudaGetLastError());
         RBFFD_CUDA_TRY(cudaMemcpyAsync(lossv.data(), m->loss, steps_per_epoch * sizeof(float),

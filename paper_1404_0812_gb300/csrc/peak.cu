@@ -34,9 +34,11 @@ extern "C" rbffd_status rbffd_fp64_peak(void* stream, double* gflops) {
     RBFFD_CUDA_TRY(cudaEventCreate(&e1));
     fp64_fma_loop<<<blocks, threads, 0, st>>>(out, 64, 0.999999, 1e-7);   // warm-up
     float best = 1e30f;
+    note_launch();
     for (int rep = 0; rep < 3; ++rep) {
         RBFFD_CUDA_TRY(cudaEventRecord(e0, st));
         fp64_fma_loop<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-7);
+        note_launch();
         RBFFD_CUDA_TRY(cudaEventRecord(e1, st));
         RBFFD_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;

@@ -31,14 +31,16 @@ struct rbffd_step_ws {
     void* vec;                     // 2 species x 7 vectors (b, r, rh, p, q, s, t)
     double* partial;               // phases x blocks x 8
     unsigned long long* bar;       // barrier counter
-    int* flags;                    // [0] error (timeout), [1] not converged, [2] has_history
+    int* flags;                    // [0] error (timeout), [1] not converged, [2] has_history,
+                                   // [3] report slot of the next step
     int* rep;                      // per step: iters_u, iters_v, failed
     double* rep_res;               // per step: relres_u, relres_v
     int64_t rep_cap;
     int blocks, threads;
-    cudaGraphExec_t graph;
-    const void* graph_key[8];
-    bool graph_ok;
+    cudaGraphExec_t graph;            // captured step (memset + launch)
+    cudaStream_t cap;                 // library-owned stream used only for capture
+    unsigned char graph_args[512];    // kernel arguments the graph holds
+    size_t graph_args_size;
 };
 
 namespace rbffd {
@@ -52,6 +54,7 @@ void step_ws_free(rbffd_step_ws* ws) {
     cudaFree(ws->rep);
     cudaFree(ws->rep_res);
     if (ws->graph) cudaGraphExecDestroy(ws->graph);
+    if (ws->cap) cudaStreamDestroy(ws->cap);
     delete ws;
 }
 
@@ -82,7 +85,6 @@ struct Args {
     int* flags;
     int* rep;
     double* rep_res;
-    int64_t rep_slot;
 };
 
 enum { VB = 0, VR = 1, VRH = 2, VP = 3, VQ = 4, VS = 5, VT = 6 };
@@ -205,6 +207,7 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool two = a.ns == 2;
     const bool hist = *((volatile int*)(a.flags + 2)) != 0;
+    const int slot = *((volatile int*)(a.flags + 3));
     unsigned long long target = 0;
     const T c0 = hist ? T(3) : T(1);
     const T cl = hist ? T(2) * a.dt : a.dt;
@@ -448,15 +451,21 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
             }
             if (fail[k]) bad = true;
         }
-        int* rp = a.rep + a.rep_slot * 3;
+        int* rp = a.rep + (int64_t)slot * 3;
         rp[0] = iters[0];
         rp[1] = iters[1];
         rp[2] = bad ? 1 : 0;
-        a.rep_res[a.rep_slot * 2] = relres[0];
-        a.rep_res[a.rep_slot * 2 + 1] = relres[1];
+        a.rep_res[(int64_t)slot * 2] = relres[0];
+        a.rep_res[(int64_t)slot * 2 + 1] = relres[1];
         if (bad) atomicExch(a.flags + 1, 1);
-        a.flags[2] = 1;   // history exists from now on
+        a.flags[2] = 1;          // history exists from now on
+        a.flags[3] = slot + 1;   // every block read the slot before the first barrier
     }
+}
+
+__global__ void lonely_barrier(unsigned long long* bar, int* err) {
+    // a second arrival never comes: the bounded wait must give up
+    grid_sync(bar, 2ull * gridDim.x, err);
 }
 
 template <typename T>
@@ -486,7 +495,6 @@ void fill_args(Args<T>& a, rbffd_op* op, rbffd_state* s, const rbffd_step_params
     a.flags = ws->flags;
     a.rep = ws->rep;
     a.rep_res = ws->rep_res;
-    a.rep_slot = 0;
 }
 
 template <typename T>
@@ -495,6 +503,45 @@ rbffd_status launch_step(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
     void* args[] = {&a};
     RBFFD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)step_kernel<T>, dim3(ws->blocks),
                                                dim3(ws->threads), args, 0, st));
+    note_launch();
+    return RBFFD_OK;
+}
+
+// nsteps launches, directly or by replaying one captured graph of a step
+template <typename T>
+rbffd_status run_steps(Args<T>& a, rbffd_step_ws* ws, int64_t nsteps, bool use_graph, cudaStream_t st) {
+    static_assert(sizeof(Args<T>) <= sizeof(ws->graph_args), "graph key too small");
+    if (!use_graph) {
+        for (int64_t k = 0; k < nsteps; ++k) {
+            rbffd_status r = launch_step(a, ws, st);
+            if (r != RBFFD_OK) return r;
+        }
+        return RBFFD_OK;
+    }
+    if (!ws->graph || ws->graph_args_size != sizeof(a) || memcmp(ws->graph_args, &a, sizeof(a)) != 0) {
+        if (ws->graph) {
+            cudaGraphExecDestroy(ws->graph);
+            ws->graph = nullptr;
+        }
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); replay on the caller's stream
+        if (!ws->cap) RBFFD_CUDA_TRY(cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        RBFFD_CUDA_TRY(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
+        rbffd_status r = launch_step(a, ws, ws->cap);
+        cudaError_t e = cudaStreamEndCapture(ws->cap, &g);
+        if (r != RBFFD_OK) return r;
+        RBFFD_CUDA_TRY(e);
+        e = cudaGraphInstantiate(&ws->graph, g, 0);
+        cudaGraphDestroy(g);
+        RBFFD_CUDA_TRY(e);
+        memcpy(ws->graph_args, &a, sizeof(a));
+        ws->graph_args_size = sizeof(a);
+    }
+    for (int64_t k = 0; k < nsteps; ++k) {
+        RBFFD_CUDA_TRY(cudaGraphLaunch(ws->graph, st));
+        note_launch();
+    }
     return RBFFD_OK;
 }
 
@@ -549,22 +596,20 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         RBFFD_CUDA_TRY(cudaMalloc(&ws->rep, ws->rep_cap * 3 * sizeof(int)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->rep_res, ws->rep_cap * 2 * sizeof(double)));
     }
-    int hflags[4] = {0, 0, s->has_history ? 1 : 0, 0};
+    int hflags[4] = {0, 0, s->has_history ? 1 : 0, 0};   // slot counter starts at 0
     RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(ws->rep, 0, ws->rep_cap * 3 * sizeof(int), st));
-    rbffd_status rs = RBFFD_OK;
-    for (int64_t k = 0; k < nsteps && rs == RBFFD_OK; ++k) {
-        if (elem == 4) {
-            Args<float> a;
-            fill_args(a, op, s, p, ws);
-            a.rep_slot = k;
-            rs = launch_step(a, ws, st);
-        } else {
-            Args<double> a;
-            fill_args(a, op, s, p, ws);
-            a.rep_slot = k;
-            rs = launch_step(a, ws, st);
-        }
+    rbffd_status rs;
+    if (elem == 4) {
+        Args<float> a;
+        memset(&a, 0, sizeof(a));
+        fill_args(a, op, s, p, ws);
+        rs = run_steps(a, ws, nsteps, p->use_graph != 0, st);
+    } else {
+        Args<double> a;
+        memset(&a, 0, sizeof(a));
+        fill_args(a, op, s, p, ws);
+        rs = run_steps(a, ws, nsteps, p->use_graph != 0, st);
     }
     if (rs != RBFFD_OK) return rs;
     std::vector<int> rep(std::max<int64_t>(nsteps, 1) * 3);
@@ -598,6 +643,29 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
     if (hflags[1]) {
         set_error("BiCGSTAB failed at step %lld", (long long)r.failed_step);
         return RBFFD_SOLVER_NOT_CONVERGED;
+    }
+    return RBFFD_OK;
+}
+
+extern "C" rbffd_status rbffd_selftest_barrier_timeout(void* stream) {
+    cudaStream_t st = as_stream(stream);
+    unsigned long long* bar = nullptr;
+    int* err = nullptr;
+    RBFFD_CUDA_TRY(cudaMalloc(&bar, sizeof(unsigned long long)));
+    RBFFD_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+    RBFFD_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned long long), st));
+    RBFFD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    lonely_barrier<<<1, 32, 0, st>>>(bar, err);
+    note_launch();
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    int h = 0;
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(bar);
+    cudaFree(err);
+    if (h) {
+        set_error("grid barrier wait gave up as designed");
+        return RBFFD_TIMEOUT;
     }
     return RBFFD_OK;
 }

@@ -181,3 +181,22 @@ def test_full_size_mixed_build_sampled(R):
         sref = ost.stencil(ns.X, int(k), n)
         e_ref, _, _ = ow.search_eps(ns.X[sref], ow.IMQ, 1e12)
         assert abs(info["eps"][k] - e_ref) <= 2e-4 + 1e-5 * e_ref
+
+
+def test_autotune_picks_a_shape_and_caches_it(R, tmp_path):
+    ns = W.fibonacci_sphere(40_000)
+    nper = W.stencil_size_groups(ns.N, (31, 50))
+    X, Nr, P = T(ns.X), T(ns.normals), T(nper, torch.int32)
+    cache = tmp_path / "tune.txt"
+    r = R.autotune_build(X, Nr, P, kernel="imq", sample=8000, cache_path=cache)
+    assert r["block_threads"] in (64, 128) and 1 <= r["blocks_per_sm"] <= 6 and r["ms"] > 0
+    r2 = R.autotune_build(X, Nr, P, kernel="imq", sample=8000, cache_path=cache)
+    assert (r2["block_threads"], r2["blocks_per_sm"]) == (r["block_threads"], r["blocks_per_sm"])
+    assert r2["ms"] == -1.0
+    # the chosen shape builds the same operator as the default one
+    a = R.build_operator(X, Nr, P, kernel="imq", kappa_target=1e12)
+    b = R.build_operator(X, Nr, P, kernel="imq", kappa_target=1e12,
+                         block_threads=r["block_threads"], blocks_per_sm=r["blocks_per_sm"])
+    ia, ib = R.get_stencil_info(a), R.get_stencil_info(b)
+    assert torch.equal(ia["eps"], ib["eps"])
+    assert torch.equal(R.get_rows(a)[1], R.get_rows(b)[1])

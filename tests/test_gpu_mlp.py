@@ -1,0 +1,92 @@
+"""GPU learned-eps network: features, forward, backward (against the float64
+oracle's analytic gradients, themselves pinned by finite differences), and
+what the trained network gains over the plain search at the same kappa_T."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as om
+from oracle import stencils as ost
+from paper_1404_0812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def T(a, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1404_0812_gb300 as R
+    R._lib.load()
+    return R
+
+
+def test_features_match_oracle(R):
+    ns = W.bumpy_sphere(5000)
+    op = R.build_operator(T(ns.X), T(ns.normals), 50, kernel="imq", kappa_target=1e12)
+    f, tgt = R.features(op, T(ns.X), T(ns.normals), 50)
+    f = f.cpu().numpy()
+    tgt = tgt.cpu().numpy()
+    eps = R.get_stencil_info(op)["eps"].cpu().numpy()
+    for k in range(0, ns.N, 211):
+        idx = ost.stencil(ns.X, k, 50)
+        fr, rs = om.features(ns.X[idx], ns.normals[idx[0]])
+        assert np.abs(f[k] - fr).max() <= 2e-6
+        assert abs(tgt[k] - np.log(eps[k] * rs)) <= 1e-5
+
+
+def test_forward_and_gradients_match_oracle(R):
+    n, B = 50, 300
+    D = 3 * n
+    p64 = W.mlp_init(D, seed=11)
+    net = R.EpsNet(n, W.mlp_pack(p64).astype(np.float32))
+    rng = np.random.default_rng(12)
+    x = rng.uniform(-1, 1, (B, D))
+    t = rng.normal(-1.0, 0.3, B)
+    x32, t32 = x.astype(np.float32), t.astype(np.float32)
+    pr = net.predict(T(x32, torch.float32)).cpu().numpy()
+    y_ref, _ = om.forward(p64, x32.astype(np.float64))
+    assert np.abs(pr - y_ref).max() <= 1e-5 * max(1.0, np.abs(y_ref).max())
+    g, loss = net.loss_grad(T(x32, torch.float32), T(t32, torch.float32))
+    l_ref, g_ref = om.loss_and_grads(p64, x32.astype(np.float64), t32.astype(np.float64))
+    assert abs(loss - l_ref) <= 1e-5 * abs(l_ref)
+    g = g.cpu().numpy()
+    g_flat = W.mlp_pack(g_ref)
+    assert np.abs(g - g_flat).max() <= 1e-4 * np.abs(g_flat).max()
+
+
+def test_training_reduces_loss_and_warm_start_saves_evaluations(R):
+    """Train on plain-search eps of a sphere and a torus (n = 50, IMQ,
+    kappa_T = 1e12), then build a held-out bumpy sphere both ways: the
+    learned start needs fewer kappa evaluations per stencil (the network is
+    accepted outright for a third or more of the held-out stencils), every accepted
+    prediction lies in the [0.5, 2] kappa_T band, and the rest still meet the
+    search's tolerance."""
+    n = 50
+    feats, tg = [], []
+    for ns in (W.fibonacci_sphere(100_000), W.torus_staggered(129)):   # 200k pairs
+        op = R.build_operator(T(ns.X), T(ns.normals), n, kernel="imq", kappa_target=1e12)
+        f, t = R.features(op, T(ns.X), T(ns.normals), n)
+        feats.append(f)
+        tg.append(t)
+    F = torch.cat(feats).contiguous()
+    Tt = torch.cat(tg).contiguous()
+    net = R.EpsNet(n, W.mlp_pack(W.mlp_init(3 * n, seed=0)).astype(np.float32))
+    losses = net.train(F, Tt, epochs=25, batch=1024, lr=1e-3, seed=0)
+    assert losses[-1] < 0.2 * losses[0]
+    test = W.bumpy_sphere(20000)
+    X, Nn = T(test.X), T(test.normals)
+    plain = R.build_operator(X, Nn, n, kernel="imq", kappa_target=1e12)
+    learned = R.build_operator(X, Nn, n, kernel="imq", kappa_target=1e12, mlps=[net])
+    ip = {k: v.cpu().numpy() for k, v in R.get_stencil_info(plain).items()}
+    il = {k: v.cpu().numpy() for k, v in R.get_stencil_info(learned).items()}
+    assert np.all(ip["status"] == 0)
+    assert np.all((il["status"] == 0) | (il["status"] == 4))
+    acc = il["status"] == 4
+    print("accepted", acc.mean(), "evals learned", il["evals"].mean(), "plain", ip["evals"].mean())
+    assert acc.mean() > 0.3
+    assert np.all((il["kappa"][acc] >= 0.5e12) & (il["kappa"][acc] <= 2e12))
+    assert np.all(np.abs(np.log(il["kappa"][~acc] / 1e12)) < 0.05)
+    assert il["evals"].mean() < 0.6 * ip["evals"].mean()

@@ -1,0 +1,196 @@
+"""GPU parity of the IMEX stepper (reaction + SBDF2 right-hand side +
+BiCGSTAB, one cooperative launch per step) against the oracle's stepper on
+the same operator.
+
+Tolerances: float64 stepping at BiCGSTAB tolerance 1e-12 matches the oracle
+to 1e-9 relative (both solve the same systems to 1e-12; the difference is
+the solver's residual times the system's conditioning).  float32 stepping is
+held to the 1e-5 relative L_inf bar against the float64 oracle on the
+horizons the parity plan names (heat equation to t = 0.1; reaction-diffusion
+over the first 100 steps)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import operator as oop
+from oracle import stepping as ostp
+from oracle import weights as ow
+from paper_1404_0812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def T(a, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def rel_inf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1404_0812_gb300 as R
+    R._lib.load()
+    return R
+
+
+def _pair(R, ns, n, kernel, kT=1e12):
+    """GPU operator (searched eps) and the oracle operator at the GPU's eps."""
+    op = R.build_operator(T(ns.X), T(ns.normals), n, kernel=kernel, kappa_target=kT)
+    eps = R.get_stencil_info(op)["eps"].cpu().numpy()
+    ref = oop.build_operator(ns.X, ns.normals, n, ow.KERNELS[kernel], eps=eps)
+    return op, ref
+
+
+def _pair_fixed(R, ns, n, kernel, eps):
+    """Both operators at one fixed eps with kappa ~ 1e6, where the two float64
+    weight computations agree to ~1e-13 even on rough fields: float64
+    stepper parity is then limited by the stepper alone.  (At kappa_T = 1e12
+    the weights of two float64 orderings differ by ~3.5e-6, which a random
+    initial state carries straight into the solution.)"""
+    e = np.full(ns.N, eps)
+    op = R.build_operator(T(ns.X), T(ns.normals), n, kernel=kernel, eps_override=T(e))
+    ref = oop.build_operator(ns.X, ns.normals, n, ow.KERNELS[kernel], eps=e)
+    return op, ref
+
+
+@pytest.fixture(scope="module")
+def sphere2562(R):
+    ns = W.icosahedral_sphere(4)
+    return (ns,) + _pair(R, ns, 31, "gaussian")
+
+
+def test_heat_equation_fp64_parity(R, sphere2562):
+    ns, op, ref = sphere2562
+    u0 = W.sph_harm_y32(ns.X)
+    p = R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=1e-4, delta_u=1.0, tol=1e-12)
+    st = R.StepState.create(T(u0))
+    rep = R.step_imex(op, st, p, 50)
+    o = ostp.imex_run(lambda x: oop.apply(ref, x), u0, None, dict(model="none", dt=1e-4, delta_u=1.0), 50)
+    assert rel_inf(st.u.cpu().numpy(), o["u"]) <= 1e-9
+    assert rep["max_iters_u"] <= 3          # Section 6: at most three iterations
+    assert st.has_history == 1 and st.step == 50
+
+
+def test_heat_equation_fp32_to_t01(R, sphere2562):
+    """Unit sphere N = 2562, n = 31, Gaussian: u0 = Y_3^2 to t = 0.1 (1000
+    steps of 1e-4) in float32 against the float64 oracle stepper, and both
+    against the exact exp(-12 t) decay."""
+    ns, op, ref = sphere2562
+    u0 = W.sph_harm_y32(ns.X)
+    p = R.StepParams(model="none", nspecies=1, dtype=torch.float32, dt=1e-4, delta_u=1.0, tol=1e-6)
+    st = R.StepState.create(T(u0, torch.float32))
+    R.step_imex(op, st, p, 1000)
+    o = ostp.imex_run(lambda x: oop.apply(ref, x), u0, None, dict(model="none", dt=1e-4, delta_u=1.0), 1000)
+    u = st.u.cpu().numpy().astype(np.float64)
+    assert rel_inf(u, o["u"]) <= 1e-5
+    exact = math.exp(-1.2) * u0
+    assert rel_inf(o["u"], exact) < 1e-3
+    assert rel_inf(u, exact) < 1e-3
+
+
+# float32: BiCGSTAB runs until the recursive residual reaches 1e-8, i.e. to the
+# float32 floor; a looser tolerance leaves tol * |b| of error per step, which
+# accumulates linearly over the 100 steps.
+@pytest.mark.parametrize("dtype,tol,bound", [(torch.float64, 1e-12, 1e-9), (torch.float32, 1e-8, 1e-5)])
+def test_schnakenberg_torus_100_steps(R, dtype, tol, bound):
+    """Two-species Schnakenberg on the staggered torus (m = 20, N = 2400),
+    n = 31, IMQ, 100 steps of dt = 0.01 from the seeded +-1% perturbation of
+    the steady state.  float64: fixed eps (kappa ~ 1e6); float32: the
+    searched kappa_T = 1e12 operator."""
+    ns = W.torus_staggered(20)
+    op, ref = _pair_fixed(R, ns, 31, "imq", 5.0) if dtype == torch.float64 else _pair(R, ns, 31, "imq")
+    s = W.SCHNAKENBERG
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    name, coef = R.model_coefs(s)
+    p = R.StepParams(model=name, nspecies=2, dtype=dtype, dt=s["dt"], delta_u=s["delta_u"],
+                     delta_v=s["delta_v"], coef=coef, tol=tol)
+    st = R.StepState.create(T(u0, dtype), T(v0, dtype))
+    R.step_imex(op, st, p, 100)
+    o = ostp.imex_run(lambda x: oop.apply(ref, x), u0, v0, s, 100)
+    assert rel_inf(st.u.cpu().numpy().astype(np.float64), o["u"]) <= bound
+    assert rel_inf(st.v.cpu().numpy().astype(np.float64), o["v"]) <= bound
+
+
+@pytest.mark.parametrize("which", ["gray_scott", "barrio"])
+def test_other_kinetics_fp64(R, which):
+    ns = W.icosahedral_sphere(3)
+    op, ref = _pair_fixed(R, ns, 31, "imq", 2.5)
+    if which == "gray_scott":
+        prm = dict(W.GRAY_SCOTT)
+        prm["delta_u"], prm["delta_v"] = 2e-4, 1e-4
+        u0, v0 = W.gray_scott_initial(ns.X, seed=5, spots=5, radius=0.3)
+    else:
+        prm = dict(W.BARRIO_SPOTS)
+        rng = np.random.default_rng(9)
+        u0, v0 = 0.01 * rng.uniform(-1, 1, ns.N), 0.01 * rng.uniform(-1, 1, ns.N)
+    name, coef = R.model_coefs(prm)
+    p = R.StepParams(model=name, nspecies=2, dtype=torch.float64, dt=prm["dt"], delta_u=prm["delta_u"],
+                     delta_v=prm["delta_v"], coef=coef, tol=1e-12)
+    st = R.StepState.create(T(u0), T(v0))
+    R.step_imex(op, st, p, 30)
+    o = ostp.imex_run(lambda x: oop.apply(ref, x), u0, v0, prm, 30)
+    assert rel_inf(st.u.cpu().numpy(), o["u"]) <= 1e-9
+    assert rel_inf(st.v.cpu().numpy(), o["v"]) <= 1e-9
+
+
+def test_split_runs_equal_one_run(R, sphere2562):
+    """History carried across calls: 10 + 15 steps equal 25 steps."""
+    ns, op, _ = sphere2562
+    u0 = W.sph_harm_y32(ns.X)
+    p = R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=1e-3, delta_u=1.0, tol=1e-12)
+    a = R.StepState.create(T(u0))
+    R.step_imex(op, a, p, 25)
+    b = R.StepState.create(T(u0))
+    R.step_imex(op, b, p, 10)
+    R.step_imex(op, b, p, 15)
+    assert torch.equal(a.u, b.u)
+
+
+def test_steady_state_and_solver_failure(R):
+    ns = W.icosahedral_sphere(3)
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="imq", kappa_target=1e12)
+    s = W.SCHNAKENBERG
+    us, vs = s["a"] + s["b"], s["b"] / (s["a"] + s["b"]) ** 2
+    name, coef = R.model_coefs(s)
+    p = R.StepParams(model=name, nspecies=2, dtype=torch.float64, dt=0.01, delta_u=s["delta_u"],
+                     delta_v=s["delta_v"], coef=coef, tol=1e-12)
+    st = R.StepState.create(T(np.full(ns.N, us)), T(np.full(ns.N, vs)))
+    R.step_imex(op, st, p, 5)
+    assert (st.u - us).abs().max().item() < 1e-10 and (st.v - vs).abs().max().item() < 1e-10
+    # an iteration cap of 1 at a tolerance it cannot meet is reported, not hidden
+    p2 = R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=0.5, delta_u=1.0, tol=1e-14,
+                      maxit=1)
+    st2 = R.StepState.create(T(W.uniform_field(ns.N, 3)))
+    rep = R.step_imex(op, st2, p2, 2, allow_failure=True)
+    assert rep["status"] == 5 and rep["failed_step"] == 0
+
+
+def test_bounded_barrier_wait_times_out(R):
+    """A barrier wait that nothing satisfies gives up after about a second
+    and reports RBFFD_TIMEOUT; the context stays usable afterwards."""
+    assert R.selftest_barrier_timeout() == 6
+    x = torch.ones(10, device="cuda")
+    assert float((x * 2).sum().item()) == 20.0
+
+
+def test_graph_replay_matches_direct_launches(R):
+    """A step captured once into a CUDA graph and replayed gives the same
+    bits as direct cooperative launches (two species, float32)."""
+    ns = W.torus_staggered(20)
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="imq", kappa_target=1e12)
+    s = W.SCHNAKENBERG
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    name, coef = R.model_coefs(s)
+    out = []
+    for g in (False, True):
+        p = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
+                         delta_v=s["delta_v"], coef=coef, tol=1e-6, use_graph=g)
+        st = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
+        R.step_imex(op, st, p, 20)
+        R.step_imex(op, st, p, 20)
+        out.append((st.u.clone(), st.v.clone()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
