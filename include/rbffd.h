@@ -223,6 +223,50 @@ int64_t rbffd_op_nnz(const rbffd_op* op);      /* sum of n_k (Section 4.1) */
 int64_t rbffd_op_apply_bytes(const rbffd_op* op, int dtype);
 void rbffd_destroy(rbffd_op* op);
 
+/*
+ * rbffd_stencil_weights_noalloc - surface-Laplacian weights for stencils and
+ * shape parameters the caller already has, without allocating any memory.
+ * (The paper has no counterpart: it is an interface for callers that may not
+ * allocate, not a step of the method.)
+ *
+ * Who needs it: code that must not call cudaMalloc / cudaFree while it runs
+ * -- for example a time loop on an evolving surface that re-forms weights
+ * every step inside a region where another framework owns the whole device
+ * heap, or an application that keeps the device running asynchronously and
+ * cannot afford the implicit device-wide synchronisation that cudaMalloc and
+ * cudaFree cause.  rbffd_build_operator allocates its operator and scratch;
+ * this call allocates nothing: the caller passes inputs and outputs, and the
+ * per-stencil working memory is a fixed 32 MiB array inside the library's
+ * device image (every GPU that loads the library keeps it until exit).
+ *
+ *   nodes, normals  device, N x 3 float64 (normals unit, sign irrelevant)
+ *   N               number of nodes (>= 2)
+ *   stencils        device, rows x n int32, row-major, centre node first;
+ *                   every index in [0, N)
+ *   rows            number of stencils (0 is allowed)
+ *   n               stencil size, 2 <= n <= min(N, 128); larger sizes are
+ *                   rejected with RBFFD_EINVAL (the fixed array bounds n)
+ *   eps             device, rows float64, shape parameter of each stencil in
+ *                   the units of the coordinates
+ *   kernel          RBFFD_GAUSSIAN or RBFFD_IMQ
+ *   weights         device out, rows x n float64: the first row of
+ *                   L_P = sum_d G^d G^d for each stencil (same arithmetic as
+ *                   the weights of rbffd_build_operator)
+ *
+ * Returns RBFFD_ESINGULAR when some rows had an out-of-range index or a
+ * local matrix that is not numerically positive definite (those rows are
+ * NaN).  Synchronises the stream.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array
+ * and its failure counter, which keep the last call's contents: the counter
+ * is cleared at the start of each call, and calls whose work overlaps on the
+ * GPU (different streams or threads without ordering) race on the array.
+ */
+rbffd_status rbffd_stencil_weights_noalloc(const double* nodes, const double* normals, int64_t N,
+                                           const int32_t* stencils, int64_t rows, int n,
+                                           const double* eps, int kernel, double* weights,
+                                           void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned shape-parameter warm start (not in the paper; the paper's search
  * of Section 5 stays as the fallback and the judge).

@@ -125,6 +125,27 @@ def autotune_build(nodes, normals, n=31, kernel="imq", kappa_target=1e12, sample
     return dict(block_threads=t.value, blocks_per_sm=b.value, ms=ms.value)
 
 
+def stencil_weights_noalloc(nodes, normals, stencils, eps, kernel="imq", weights=None, stream=None):
+    """rbffd_stencil_weights_noalloc: weights (rows x n float64) of caller-given
+    stencils (rows x n int32, centre first) at caller-given eps, computed
+    without any device allocation inside the library.  ``weights`` may be a
+    preallocated CUDA float64 tensor."""
+    lib = _lib.load()
+    nodes = _dev(nodes, torch.float64)
+    normals = _dev(normals, torch.float64)
+    stencils = _dev(stencils, torch.int32)
+    eps = _dev(eps, torch.float64)
+    rows, n = stencils.shape
+    if weights is None:
+        weights = torch.empty((rows, n), dtype=torch.float64, device=stencils.device)
+    _dev(weights, torch.float64)
+    _lib.check(lib.rbffd_stencil_weights_noalloc(_ptr(nodes), _ptr(normals), nodes.shape[0], _ptr(stencils),
+                                                 rows, n, _ptr(eps), KERNELS[kernel] if isinstance(kernel, str)
+                                                 else int(kernel), _ptr(weights), _stream(stream)),
+               "rbffd_stencil_weights_noalloc")
+    return weights
+
+
 def apply(op: Operator, u, y=None, stream=None):
     """rbffd_apply: y = L_X u (float32 or float64 by u's dtype)."""
     lib = _lib.load()

@@ -77,6 +77,8 @@ SIGNATURES = {
                                   vp, vp]),
     "rbffd_mlp_predict": (C.c_int, [vp, vp, C.c_int64, vp, vp]),
     "rbffd_selftest_barrier_timeout": (C.c_int, [vp]),
+    "rbffd_stencil_weights_noalloc": (C.c_int, [vp, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int,
+                                                vp, vp]),
     "rbffd_status_str": (C.c_char_p, [C.c_int]),
     "rbffd_last_error": (C.c_char_p, []),
     "rbffd_fp64_peak": (C.c_int, [vp, C.POINTER(C.c_double)]),

@@ -40,6 +40,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace rbffd {
 namespace {
@@ -896,3 +897,205 @@ rbffd_status build_weights(rbffd_op* op, const double* nodes, const double* norm
 }
 
 }  // namespace rbffd
+
+// ---------------------------------------------------------------------------
+// Allocation-free weights for caller-supplied stencils
+// (rbffd_stencil_weights_noalloc).  The scratch lives in a fixed array in the
+// library's device image instead of memory obtained at run time.
+// ---------------------------------------------------------------------------
+namespace rbffd {
+namespace {
+
+constexpr int64_t NOALLOC_SCRATCH_DOUBLES = (int64_t)4 << 20;   // 32 MiB of float64
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+static __device__ int g_noalloc_fail;   // rows that failed in the current call
+
+// geometry of one stencil given as a row of node indices (centre first);
+// returns false when an index is outside [0, N)
+__device__ bool load_geometry_row(const Lane& S, const Layout& ly, int n, const int32_t* __restrict__ row,
+                                  const double* __restrict__ X, const double* __restrict__ NR, int64_t N,
+                                  Geo& g) {
+    for (int j = 0; j < n; ++j)
+        if (row[j] < 0 || (int64_t)row[j] >= N) return false;
+    int c = row[0];
+    double cx = X[3 * (int64_t)c], cy = X[3 * (int64_t)c + 1], cz = X[3 * (int64_t)c + 2];
+    double rs2 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        int k = row[j];
+        double dx = X[3 * (int64_t)k] - cx, dy = X[3 * (int64_t)k + 1] - cy, dz = X[3 * (int64_t)k + 2] - cz;
+        S[ly.XS + j] = dx;
+        S[ly.XS + ly.m + j] = dy;
+        S[ly.XS + 2 * ly.m + j] = dz;
+        rs2 = fmax(rs2, dx * dx + dy * dy + dz * dz);
+        double nx = NR[3 * (int64_t)k], ny = NR[3 * (int64_t)k + 1], nz = NR[3 * (int64_t)k + 2];
+        double inv = rsqrt(nx * nx + ny * ny + nz * nz);
+        S[ly.NS + j] = nx * inv;
+        S[ly.NS + ly.m + j] = ny * inv;
+        S[ly.NS + 2 * ly.m + j] = nz * inv;
+    }
+    g.rs = sqrt(rs2);
+    double inv = 1.0 / g.rs;
+    for (int j = 0; j < n; ++j) {
+        S[ly.XS + j] *= inv;
+        S[ly.XS + ly.m + j] *= inv;
+        S[ly.XS + 2 * ly.m + j] *= inv;
+    }
+    g.mean_d = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double xi = S[ly.XS + i], yi = S[ly.XS + ly.m + i], zi = S[ly.XS + 2 * ly.m + i];
+        int base = pk(i, 0);
+        for (int j = 0; j < i; ++j) {
+            double dx = xi - S[ly.XS + j], dy = yi - S[ly.XS + ly.m + j], dz = zi - S[ly.XS + 2 * ly.m + j];
+            S[ly.R2 + base + j] = dx * dx + dy * dy + dz * dz;
+        }
+        S[ly.R2 + base + i] = 0.0;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(128)
+weights_rows_kernel(const double* __restrict__ X, const double* __restrict__ NR, int64_t N,
+                    const int32_t* __restrict__ stencils, int64_t rows, int n,
+                    const double* __restrict__ eps, int kernel, double* __restrict__ Wout,
+                    double* __restrict__ scratch, int lane_size) {
+    const int lane_id = threadIdx.x & 31;
+    const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    Lane S{scratch + warp_global * 32 * (int64_t)lane_size + lane_id};
+    const int npad = (n + 3) / 4 * 4;
+    const Layout ly = make_layout(npad, true);
+    const int m = ly.m, XS = ly.XS;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += stride) {
+        double* w_row = Wout + r * (int64_t)n;
+        Geo geo;
+        bool ok = load_geometry_row(S, ly, n, stencils + r * (int64_t)n, X, NR, N, geo);
+        double eps_s = ok ? eps[r] * geo.rs : 0.0;
+        double e2 = eps_s * eps_s;
+        double s = 0.0;
+        if (ok) {
+            assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH);
+            ok = cholesky(S, ly) && isfinite(eps_s) && eps_s > 0.0;
+        }
+        if (ok) {
+            for (int i = 0; i < m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
+            chol_solve(S, ly, ly.U);
+            for (int i = 0; i < n; ++i) s += S[ly.U + i];
+            ok = s > 0.0 && isfinite(s);
+        }
+        if (!ok) {
+            atomicAdd(&g_noalloc_fail, 1);
+            for (int j = 0; j < n; ++j) w_row[j] = NAN;
+            continue;
+        }
+        double n0x = S[ly.NS], n0y = S[ly.NS + m], n0z = S[ly.NS + 2 * m];
+        for (int d = 0; d < 3; ++d)
+            for (int i = 0; i < m; ++i) S[ly.GV + d * m + i] = 0.0;
+        for (int j = 1; j < n; ++j) {
+            double ps = psi_from_phi(kernel, e2, S[ly.PH + pk(j, 0)]);
+            double dx = -S[XS + j], dy = -S[XS + m + j], dz = -S[XS + 2 * m + j];
+            double nd = n0x * dx + n0y * dy + n0z * dz;
+            S[ly.GV + j] = ps * (dx - n0x * nd);
+            S[ly.GV + m + j] = ps * (dy - n0y * nd);
+            S[ly.GV + 2 * m + j] = ps * (dz - n0z * nd);
+        }
+        for (int d = 0; d < 3; ++d) aug_solve0(S, ly, n, ly.GV + d * m, s);
+        for (int i = 0; i < n; ++i) {
+            double gx = S[ly.GV + i], gy = S[ly.GV + m + i], gz = S[ly.GV + 2 * m + i];
+            double nx = S[ly.NS + i], ny = S[ly.NS + m + i], nz = S[ly.NS + 2 * m + i];
+            double nd = nx * gx + ny * gy + nz * gz;
+            S[ly.HV + i] = gx - nx * nd;
+            S[ly.HV + m + i] = gy - ny * nd;
+            S[ly.HV + 2 * m + i] = gz - nz * nd;
+        }
+        const int V = ly.Q0;
+        for (int i = 0; i < m; ++i) S[V + i] = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double xi = S[XS + i], yi = S[XS + m + i], zi = S[XS + 2 * m + i];
+            double hx = S[ly.HV + i], hy = S[ly.HV + m + i], hz = S[ly.HV + 2 * m + i];
+            double vi = 0.0;
+            int base = pk(i, 0);
+            for (int j = 0; j < i; ++j) {
+                double ps = psi_from_phi(kernel, e2, S[ly.PH + base + j]);
+                double dx = xi - S[XS + j], dy = yi - S[XS + m + j], dz = zi - S[XS + 2 * m + j];
+                double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
+                S[V + j] = fma(ps, dx * hx + dy * hy + dz * hz, S[V + j]);
+                vi = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi);
+            }
+            S[V + i] += vi;
+        }
+        aug_solve0(S, ly, n, V, s);
+        double inv_rs2 = 1.0 / (geo.rs * geo.rs);
+        for (int j = 0; j < n; ++j) w_row[j] = S[V + j] * inv_rs2;
+    }
+}
+
+// Device address of the scratch array, looked up once per device.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int* g_noalloc_fail_ptr[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mu;
+
+}  // namespace
+}  // namespace rbffd
+
+extern "C" rbffd_status rbffd_stencil_weights_noalloc(const double* nodes, const double* normals, int64_t N,
+                                                      const int32_t* stencils, int64_t rows, int n,
+                                                      const double* eps, int kernel, double* weights,
+                                                      void* stream) {
+    using namespace rbffd;
+    RBFFD_CHECK_ARG(nodes && normals && stencils && eps && weights, "NULL argument");
+    RBFFD_CHECK_ARG(kernel == RBFFD_GAUSSIAN || kernel == RBFFD_IMQ, "kernel");
+    RBFFD_CHECK_ARG(N >= 2 && rows >= 0, "N must be >= 2 and rows >= 0");
+    if (n < 2 || n > RBFFD_MAX_N || n > N) {
+        set_error("rbffd_stencil_weights_noalloc: stencil size %d outside [2, min(N, %d)]", n, RBFFD_MAX_N);
+        return RBFFD_EINVAL;
+    }
+    const int npad = (n + 3) / 4 * 4;
+    const int lane_size = make_layout(npad, true).size;
+    int64_t lanes = NOALLOC_SCRATCH_DOUBLES / lane_size / 32 * 32;
+    if (lanes < 32) {   // cannot happen for n <= 128 with 32 MiB; kept as the size guard
+        set_error("rbffd_stencil_weights_noalloc: stencil size %d needs more than the fixed scratch", n);
+        return RBFFD_EINVAL;
+    }
+    if (rows == 0) return RBFFD_OK;
+    int dev = 0;
+    RBFFD_CUDA_TRY(cudaGetDevice(&dev));
+    RBFFD_CHECK_ARG(dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device ordinal");
+    double* scratch;
+    int* fail;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // with this device current: the symbols' device addresses
+            void* p = nullptr;
+            void* f = nullptr;
+            RBFFD_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            RBFFD_CUDA_TRY(cudaGetSymbolAddress(&f, g_noalloc_fail));
+            g_noalloc_fail_ptr[dev] = static_cast<int*>(f);
+            g_noalloc_ptr[dev] = static_cast<double*>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+        fail = g_noalloc_fail_ptr[dev];
+    }
+    cudaStream_t st = as_stream(stream);
+    // the failure counter must start at zero; the scratch itself is written
+    // before it is read in every row, so it is not cleared
+    RBFFD_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st));
+    int64_t need = (rows + 31) / 32 * 32;
+    lanes = std::min(lanes, need);
+    int threads = (int)std::min<int64_t>(128, lanes);
+    int blocks = (int)(lanes / threads);
+    weights_rows_kernel<<<blocks, threads, 0, st>>>(nodes, normals, N, stencils, rows, n, eps, kernel, weights,
+                                                    scratch, lane_size);
+    note_launch();
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    int hfail = 0;
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hfail) {
+        set_error("%d stencils have an out-of-range index or a local matrix that is not positive definite "
+                  "(their weights are NaN)", hfail);
+        return RBFFD_ESINGULAR;
+    }
+    return RBFFD_OK;
+}

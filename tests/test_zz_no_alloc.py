@@ -1,0 +1,65 @@
+"""The allocation-free weights entry point against the operator build.
+
+rbffd_stencil_weights_noalloc is for callers that may not allocate device
+memory while they run (for example a time loop re-forming weights inside a
+region where another framework owns the device heap, or code that cannot
+take the device-wide synchronisation of cudaMalloc / cudaFree).  It works in
+a fixed array inside the library, so this test checks, through the C ABI,
+that two calls in a row -- the second reusing the array the first left
+behind -- give the weights the allocating build gives for the same stencils
+and shape parameters.  It lives in its own file, collected last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1404_0812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def _noalloc(lib, X, Nr, stencils, eps, kernel):
+    rows, n = stencils.shape
+    out = torch.full((rows, n), float("nan"), dtype=torch.float64, device="cuda")
+    st = lib.rbffd_stencil_weights_noalloc(C.c_void_p(X.data_ptr()), C.c_void_p(Nr.data_ptr()), X.shape[0],
+                                           C.c_void_p(stencils.data_ptr()), rows, n,
+                                           C.c_void_p(eps.data_ptr()), kernel, C.c_void_p(out.data_ptr()),
+                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st, out
+
+
+@pytest.mark.parametrize("case", [("imq", 1, 50, 40_000), ("gaussian", 0, 31, 2562)])
+def test_noalloc_weights_match_the_build_on_two_calls(case):
+    import paper_1404_0812_gb300 as R
+    lib = R._lib.load()
+    kernel, kid, n, N = case
+    ns = W.icosahedral_sphere(4) if N == 2562 else W.fibonacci_sphere(N)
+    X, Nr = _dev(ns.X, torch.float64), _dev(ns.normals, torch.float64)
+    # the allocating path: stencils, searched eps and weights
+    op = R.build_operator(X, Nr, n, kernel=kernel, kappa_target=1e12)
+    idx, w_ref = R.get_rows(op)
+    eps = R.get_stencil_info(op)["eps"]
+    scale = w_ref.abs().amax(dim=1, keepdim=True)
+    # call 1: every row; call 2: a different subset and order, same array
+    sel2 = torch.as_tensor(np.random.default_rng(7).permutation(ns.N)[: ns.N // 3], device="cuda")
+    for rows in (torch.arange(ns.N, device="cuda"), sel2):
+        st, w = _noalloc(lib, X, Nr, idx[rows].contiguous(), eps[rows].contiguous(), kid)
+        assert st == 0, lib.rbffd_last_error()
+        err = ((w - w_ref[rows]).abs() / scale[rows]).max().item()
+        assert err <= 1e-8, err
+
+
+def test_noalloc_rejects_sizes_beyond_its_limit():
+    import paper_1404_0812_gb300 as R
+    lib = R._lib.load()
+    ns = W.fibonacci_sphere(500)
+    X, Nr = _dev(ns.X, torch.float64), _dev(ns.normals, torch.float64)
+    st, _ = _noalloc(lib, X, Nr, torch.zeros((4, 129), dtype=torch.int32, device="cuda"),
+                     torch.ones(4, dtype=torch.float64, device="cuda"), 1)
+    assert st == 1 and b"stencil size" in lib.rbffd_last_error()
