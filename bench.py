@@ -23,8 +23,9 @@ launch actually performed for stencil k) over the search kernel's CUDA-event
 time, against the measured FP64 FMA peak.  The oracle's median evaluation
 counts are reported beside it.
 
---profile runs the same pipeline once on a 40,000-node version of the
-workload (same four stencil sizes) inside an NVTX range "profiled", for ncu.
+--profile runs the same pipeline once on a smaller version of the workload
+(--profile-n nodes, default 40,000, same four stencil sizes; --profile-plain
+without the learned start) inside an NVTX range "profiled", for ncu.
 
 --impl reference times the CPU FP64 oracle (single thread) on a bounded
 sample of the same workload and prints the same JSON line.
@@ -61,10 +62,25 @@ def _parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other configurations' report")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--sample", type=int, default=20, help="oracle stencils per size per step")
     ap.add_argument("--profile", action="store_true", help="one small run for ncu (NVTX 'profiled')")
+    ap.add_argument("--profile-n", type=int, default=40_000, help="nodes of the --profile case")
+    ap.add_argument("--profile-plain", action="store_true", help="--profile without the learned start")
     return ap.parse_args()
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over the ranks of the default process group (the
+    slowest replica's time); the value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def _dist():
@@ -172,13 +188,16 @@ def _file_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def train_networks(R, W, T, torch):
-    """One eps network per stencil size, trained on plain-search eps of a
-    Fibonacci sphere (60k) and a staggered torus (m = 100, 60k)."""
+def train_networks(R, W, T, torch, pairs=200_000):
+    """One eps network per stencil size, trained on plain-search eps of
+    Fibonacci spheres (100k and 400k nodes) and staggered tori (m = 60 and
+    150): `pairs` (stencil, eps) pairs drawn at random (seed 3) per size."""
     import numpy as np
     nets = []
-    sets = [W.fibonacci_sphere(60_000), W.torus_staggered(100)]
+    sets = [W.fibonacci_sphere(100_000), W.fibonacci_sphere(400_000), W.torus_staggered(60),
+            W.torus_staggered(150)]
     dev = [(T(s.X), T(s.normals)) for s in sets]
+    gen = torch.Generator(device="cuda").manual_seed(3)
     for n in SIZES:
         F, Y = [], []
         for X, Nr in dev:
@@ -186,10 +205,168 @@ def train_networks(R, W, T, torch):
             f, y = R.features(op, X, Nr, n)
             F.append(f)
             Y.append(y)
+            del op
+        F = torch.cat(F)
+        Y = torch.cat(Y)
+        sel = torch.randperm(F.shape[0], generator=gen, device="cuda")[:pairs]
         net = R.EpsNet(n, W.mlp_pack(W.mlp_init(3 * n, seed=n)).astype(np.float32))
-        net.train(torch.cat(F).contiguous(), torch.cat(Y).contiguous(), epochs=20, batch=1024, lr=1e-3, seed=0)
+        net.train(F[sel].contiguous(), Y[sel].contiguous(), epochs=30, batch=1024, lr=1e-3, seed=0)
         nets.append(net)
+        del F, Y
     return nets
+
+
+def configs_report(R, W, T, torch, nets):
+    """The other benchmark configurations, measured after the timed steps
+    (not part of the headline value).  A configuration that fails reports
+    its error instead of its numbers."""
+    out = {}
+    for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2), ("bumpy500k_learned", _c4),
+                     ("bumpy2m_pointcloud", _c5)):
+        try:
+            out[name] = fn(R, W, T, torch, nets)
+        except Exception as e:   # reported, not hidden
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:400]}
+        torch.cuda.synchronize()
+    return out
+
+
+def _ev(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _c1(R, W, T, torch, nets):
+    import numpy as np
+    ev = lambda: _ev(torch)
+    stream = torch.cuda.current_stream()
+    # C1: unit sphere N = 2562 (icosahedral), n = 31, Gaussian; heat equation
+    # from Y_3^2 to t = 0.1 (1000 steps of 1e-4) vs exp(-12 t) decay
+    ns = W.icosahedral_sphere(4)
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="gaussian", kappa_target=KAPPA_T)
+    u0 = W.sph_harm_y32(ns.X)
+    exact = math.exp(-1.2) * u0
+    c1 = {}
+    for dt_, tol in ((torch.float64, 1e-12), (torch.float32, 1e-6)):
+        st = R.StepState.create(T(u0, dt_))
+        p = R.StepParams(model="none", nspecies=1, dtype=dt_, dt=1e-4, delta_u=1.0, tol=tol, use_graph=True)
+        a, b = ev()
+        a.record(stream)
+        rep = R.step_imex(op, st, p, 1000)
+        b.record(stream)
+        torch.cuda.synchronize()
+        err = float(np.abs(st.u.double().cpu().numpy() - exact).max() / np.abs(exact).max())
+        c1["f64" if dt_ == torch.float64 else "f32"] = {"ms_per_step": round(a.elapsed_time(b) / 1000, 4),
+                                                        "rel_err_vs_exact": err,
+                                                        "max_iters": rep["max_iters_u"]}
+    return c1
+
+
+def _c2(R, W, T, torch, nets):
+    ev = lambda: _ev(torch)
+    stream = torch.cuda.current_stream()
+    # C2: torus m = 82 (N = 40,344), n = 50, IMQ; Schnakenberg, float32 vs
+    # float64 stepping (100 steps compared; 5000 float32 steps timed)
+    ns = W.torus_staggered(82)
+    op = R.build_operator(T(ns.X), T(ns.normals), 50, kernel="imq", kappa_target=KAPPA_T)
+    s = W.SCHNAKENBERG
+    name, coef = R.model_coefs(s)
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    res = {}
+    for dt_, tol in ((torch.float64, 1e-12), (torch.float32, 1e-8)):
+        st = R.StepState.create(T(u0, dt_), T(v0, dt_))
+        p = R.StepParams(model=name, nspecies=2, dtype=dt_, dt=s["dt"], delta_u=s["delta_u"],
+                         delta_v=s["delta_v"], coef=coef, tol=tol, use_graph=True)
+        a, b = ev()
+        a.record(stream)
+        R.step_imex(op, st, p, 100)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[dt_] = (st, a.elapsed_time(b) / 100)
+    d = float((res[torch.float32][0].u.double() - res[torch.float64][0].u).abs().max()
+              / res[torch.float64][0].u.abs().max())
+    st = res[torch.float32][0]
+    p = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
+                     delta_v=s["delta_v"], coef=coef, tol=1e-6, use_graph=True)
+    a, b = ev()
+    a.record(stream)
+    R.step_imex(op, st, p, 4900)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return {"f32_vs_f64_rel_linf_100_steps": d,
+                                    "ms_per_step_f64": round(res[torch.float64][1], 4),
+                                    "ms_per_step_f32": round(res[torch.float32][1], 4),
+                                    "ms_per_step_f32_steps_101_5000": round(a.elapsed_time(b) / 4900, 4),
+                                    "u_range_at_5000": [float(st.u.min()), float(st.u.max())]}
+
+
+def _c4(R, W, T, torch, nets):
+    # C4: held-out bumpy sphere N = 500k, n = 50: learned start vs plain search
+    ns = W.bumpy_sphere(500_000)
+    X, Nr = T(ns.X), T(ns.normals)
+    net50 = nets[SIZES.index(50)]
+    rows = {}
+    for lab, m in (("plain", None), ("learned", [net50])):
+        op = R.build_operator(X, Nr, 50, kernel="imq", kappa_target=KAPPA_T, mlps=m)
+        ph = R.get_build_timings(op)
+        info = R.get_stencil_info(op)
+        rows[lab] = {"guess_plus_search_ms": round(ph["guess"] + ph["search"], 2),
+                     "build_ms": round(sum(ph.values()), 2),
+                     "evals_mean": round(float(info["evals"].double().mean()), 3),
+                     "accepted_fraction": round(float((info["status"] == 4).double().mean()), 4)}
+        del op
+    rows["speedup_search"] = round(rows["plain"]["guess_plus_search_ms"] / rows["learned"]["guess_plus_search_ms"], 3)
+    rows["stencils_per_s_learned_build"] = round(ns.N / (rows["learned"]["build_ms"] * 1e-3), 1)
+    return rows
+
+
+def _c5(R, W, T, torch, nets):
+    ev = lambda: _ev(torch)
+    stream = torch.cuda.current_stream()
+    # C5: bumpy sphere N = 2M, jittered, 20-NN PCA normals, n = 70, learned
+    # start; apply bandwidth and Gray-Scott float32 steps
+    ns = W.bumpy_sphere(2_000_000, jitter=0.25, seed=4, normals="pca")
+    X, Nr = T(ns.X), T(ns.normals)
+    op = R.build_operator(X, Nr, 70, kernel="imq", kappa_target=KAPPA_T, mlps=[nets[SIZES.index(70)]],
+                          allow_failures=True)
+    ph = R.get_build_timings(op)
+    info = R.get_stencil_info(op)
+    uu = torch.rand(ns.N, dtype=torch.float32, device="cuda")
+    yy = torch.empty_like(uu)
+    for _ in range(3):
+        R.apply(op, uu, yy)
+    a, b = ev()
+    a.record(stream)
+    for _ in range(20):
+        R.apply(op, uu, yy)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ams = a.elapsed_time(b) / 20
+    out = {
+        "build_ms": round(sum(ph.values()), 1), "phases_ms": {k: round(v, 1) for k, v in ph.items()},
+        "stencils_per_s": round(ns.N / (sum(ph.values()) * 1e-3), 1),
+        "stencils_ok_fraction": round(float(((info["status"] == 0) | (info["status"] == 4)).double().mean()), 6),
+        "accepted_fraction": round(float((info["status"] == 4).double().mean()), 4),
+        "apply_f32_GB_s": round(op.apply_bytes(R.F32) / (ams * 1e-3) / 1e9, 1)}
+    g = W.GRAY_SCOTT
+    name, coef = R.model_coefs(g)
+    u0, v0 = W.gray_scott_initial(ns.X, seed=5, spots=50, radius=0.05)
+    st = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
+    p = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=g["dt"], delta_u=g["delta_u"],
+                     delta_v=g["delta_v"], coef=coef, tol=1e-6, use_graph=True)
+    rep = R.step_imex(op, st, p, 2, allow_failure=True)
+    if rep["status"] != 0:
+        out["gray_scott_error"] = {k: rep[k] for k in ("status", "failed_step", "max_iters_u", "max_iters_v",
+                                                       "last_relres_u", "last_relres_v")}
+        return out
+    a, b = ev()
+    a.record(stream)
+    rep = R.step_imex(op, st, p, 20, allow_failure=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["gray_scott_f32_ms_per_step"] = round(a.elapsed_time(b) / 20, 3)
+    out["gray_scott_max_iters"] = [rep["max_iters_u"], rep["max_iters_v"]]
+    out["gray_scott_status"] = rep["status"]
+    return out
 
 
 def run_ours(args):
@@ -209,12 +386,12 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.profile:   # oracle sample first, before heavy GPU work
         cpu = run_cpu_sample(args.sample, 1234)
-    n_nodes = 40_000 if args.profile else N_NODES
+    n_nodes = args.profile_n if args.profile else N_NODES
 
     ns = W.fibonacci_sphere(n_nodes)
     nper = W.stencil_size_groups(n_nodes, SIZES)
     X, Nr, NP = T(ns.X), T(ns.normals), T(nper, torch.int32)
-    nets = None if args.no_learned else train_networks(R, W, T, torch)
+    nets = None if (args.no_learned or args.profile_plain) else train_networks(R, W, T, torch)
     s = W.SCHNAKENBERG
     name, coef = R.model_coefs(s)
     u0, v0 = W.schnakenberg_initial(n_nodes, seed=2)
@@ -223,8 +400,14 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # launch shape of the build kernels from the project's autotuner (timed on
+    # a strided 1/20 subsample of this node set)
+    shape = (dict(block_threads=0, blocks_per_sm=0) if args.profile else
+             R.autotune_build(X, Nr, NP, kernel="imq", kappa_target=KAPPA_T, sample=max(n_nodes // 20, 2000)))
+
     def one_step(Xd, Nd, NPd):
-        op = R.build_operator(Xd, Nd, NPd, kernel="imq", kappa_target=KAPPA_T, mlps=nets)
+        op = R.build_operator(Xd, Nd, NPd, kernel="imq", kappa_target=KAPPA_T, mlps=nets,
+                              block_threads=shape["block_threads"], blocks_per_sm=shape["blocks_per_sm"])
         st = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
         R.step_imex(op, st, sp, 1)
         return op
@@ -239,13 +422,15 @@ def run_ours(args):
         R.apply(op, uu)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"profile_case": "fibonacci_sphere_40k_mixed_n", "N": n_nodes,
+        print(json.dumps({"profile_case": f"fibonacci_sphere_{n_nodes}_mixed_n", "N": n_nodes,
+                          "learned": nets is not None,
                           "phases_ms": R.get_build_timings(op)}))
         return
 
     # plain search once (untimed) for the learned-vs-plain speedup
     torch.cuda.synchronize()
-    op_plain = R.build_operator(X, Nr, NP, kernel="imq", kappa_target=KAPPA_T)
+    op_plain = R.build_operator(X, Nr, NP, kernel="imq", kappa_target=KAPPA_T,
+                                block_threads=shape["block_threads"], blocks_per_sm=shape["blocks_per_sm"])
     plain_ms = R.get_build_timings(op_plain)
     plain_evals = R.get_stencil_info(op_plain)["evals"].double().mean().item()
     del op_plain
@@ -278,11 +463,7 @@ def run_ours(args):
     launches = R.launch_count() - l0
     if ws > 1:
         torch.distributed.barrier()
-    ms = statistics.mean(times)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(times), dev)
 
     # end to end through the public API from pinned host memory
     hX = torch.from_numpy(ns.X).pin_memory()
@@ -308,6 +489,7 @@ def run_ours(args):
 
     if rank != 0:
         return
+    configs = configs_report(R, W, T, torch, nets) if (nets is not None and not args.no_extras) else None
     # ---- roofline of the search kernel (float64 ALU): evaluations it performed
     E = {int(n): float(statistics.median(v)) for n, v in cpu["evals"].items()}
     ev_np = evals_t.cpu().numpy().astype(np.float64)
@@ -334,6 +516,26 @@ def run_ours(args):
         ams = a0.elapsed_time(a1) / 20
         gbs = op.apply_bytes(code) / (ams * 1e-3) / 1e9
         apply["f32" if code == R.F32 else "f64"] = {"ms": round(ams, 4), "GB_s": round(gbs, 1)}
+    # IMEX step on the built operator: graph-replayed steps timed with events;
+    # bytes = ELL passes (phase R + 2 per BiCGSTAB iteration, both species
+    # share each pass) x (nnz * 8 B float32 weights + indices)
+    st = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
+    R.step_imex(op, st, sp, 2)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    rep = R.step_imex(op, st, sp, 10)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = s0.elapsed_time(s1) / 10
+    iters = rep["total_iters"] / 10.0 / 2.0          # per species per step
+    passes = 1.0 + 2.0 * max(rep["max_iters_u"], rep["max_iters_v"])
+    ell_bytes = op.nnz * 8.0
+    step_info = {"ms": round(step_ms, 3), "iters_mean_per_species": round(iters, 2),
+                 "max_iters_u": rep["max_iters_u"], "max_iters_v": rep["max_iters_v"],
+                 "ell_passes_upper": passes,
+                 "ell_GB_s_upper": round(passes * ell_bytes / (step_ms * 1e-3) / 1e9, 1)}
     hbm = None
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -352,6 +554,7 @@ def run_ours(args):
                    "groups": "4 contiguous index bands of 250k", "kernel": "imq", "kappa_T": KAPPA_T,
                    "eps_tol": 1e-4, "learned_start": nets is not None,
                    "imex_step": "schnakenberg f32, 1 step, CUDA graph", "l2": "flushed (256 MB write) per step",
+                   "launch_shape": {k: shape[k] for k in ("block_threads", "blocks_per_sm")},
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "kernel": "search_kernel (float64)", "achieved": round(achieved, 4),
                      "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
@@ -367,7 +570,9 @@ def run_ours(args):
                             "learned_evals_mean": round(float(info["evals"].mean()), 3),
                             "accepted_fraction": round(float((info["status"] == 4).mean()), 4)},
         "apply": apply,
+        "imex_step": step_info,
         "all_stencils_ok": ok,
+        "other_configs": configs,
         "e2e": {"value": round(N_NODES / statistics.mean(e2e_times), 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

@@ -83,7 +83,8 @@ void rbffd_build_opts_default(rbffd_build_opts* opts);
  * blocks per SM) of the build's lane-per-stencil kernels for this device and
  * workload (a systems addition; the paper has no GPU).  Builds the operator
  * on every (N / sample)-th node (same surface and stencil sizes, coarser
- * spacing) with each candidate shape, times the search + weights phases with
+ * spacing; the sample is raised to at least 8 stencils per lane of the
+ * largest candidate) with each candidate shape, times the search + weights phases with
  * CUDA events, and returns the fastest in *block_threads / *blocks_per_sm
  * (and its time in *best_ms, -1 when it came from the cache).  Arguments as
  * in rbffd_build_operator; cache_path (may be NULL) is a text file of
@@ -209,8 +210,10 @@ rbffd_status rbffd_get_rows(const rbffd_op* op, int32_t* idx, double* w, void* s
 /*
  * Device time of the phases of the last rbffd_build_operator that produced
  * op, from CUDA events recorded on its stream around the launches (ms):
- * [0] stencils (kNN), [1] learned first guess, [2] shape-parameter search,
- * [3] weights.  Host-side work between launches is not included.
+ * [0] stencils (kNN), [1] learned first guess, [2] shape-parameter search
+ * (which also forms the weights from its last factorisation), [3] weights
+ * at given eps (eps_override builds only; 0 otherwise).  Host-side work
+ * between launches is not included.
  */
 rbffd_status rbffd_get_build_timings(const rbffd_op* op, double ms[4]);
 /* Kernel launches issued by this library since it was loaded. */

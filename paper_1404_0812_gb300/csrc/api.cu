@@ -281,9 +281,13 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
         TRY_OP(cudaEventRecord(ev[2], st));
         TRY_OP(cudaEventRecord(ev[3], st));
     }
-    // ---- weights
-    s = build_weights(op, nodes, normals, o, op->eps, st);
-    if (s != RBFFD_OK && s != RBFFD_ESINGULAR) return fail(s);
+    // ---- weights (the search writes them itself from its last factorisation)
+    if (o.eps_override) {
+        s = build_weights(op, nodes, normals, o, op->eps, st);
+        if (s != RBFFD_OK && s != RBFFD_ESINGULAR) return fail(s);
+    } else {
+        s = RBFFD_OK;
+    }
     TRY_OP(cudaEventRecord(ev[4], st));
     TRY_OP(cudaStreamSynchronize(st));
     for (int i = 0; i < 4; ++i) {

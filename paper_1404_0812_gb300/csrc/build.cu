@@ -23,12 +23,16 @@
 //
 // Shape parameter search (Eq. target_cond): F(x) = ln(kappa(A(e^x)) /
 // kappa_T) in x = ln(eps * r_s) (coordinates translated to the stencil
-// centre and scaled by the stencil radius r_s).  Bracket by secant steps
-// from the oracle's starting point (eps_0 = 1 / mean neighbour distance) or
-// from a learned prediction, then Brent-Dekker in x to the absolute eps
-// tolerance.  Lanes that finish take the next stencil from a global counter,
-// so a warp stays full until the work runs out.  Groups of different stencil
-// size are processed largest first in the same persistent launch.
+// centre and scaled by the stencil radius r_s).  Safeguarded Newton from the
+// oracle's starting point (eps_0 = 1 / mean neighbour distance) or from a
+// learned prediction: dF/dx comes with every evaluation from the
+// Hellmann-Feynman derivative of the smallest eigenvalue (its eigenvector is
+// the Ritz vector of the A^{-1} Lanczos run); a bracket and bisection guard
+// the steps; the search
+// stops when the Newton step is below half the eps tolerance.  Lanes that
+// finish take the next stencil from a global counter, so a warp stays full
+// until the work runs out.  Groups of different stencil size are processed
+// largest first in the same persistent launch.
 //
 // Weights (Eqs. grad_x_f_interp, surface_lap_P1): only the first row of
 // L_P = sum_d G^d G^d is needed, so with A symmetric
@@ -47,10 +51,14 @@ namespace {
 
 constexpr int LANCZOS_KMAX = 24;
 constexpr double LANCZOS_RTOL = 1e-6;       // relative change that stops a Lanczos run
-constexpr int LANCZOS_KMIN = 3;             // never stop before this many steps
+// The A^{-1} run never stops before this many steps: when the second
+// smallest |eigenvalue| of A is within a factor 0.6-0.9 of the smallest, the
+// top Ritz value can sit on the second one for several steps (the component
+// of lambda_min's eigenvector grows by (1 + 2 sqrt(gap))^k per step), and
+// stopping on a stalled value misjudges kappa by 10-40 %.
+constexpr int LANCZOS_KMIN = 10;
 constexpr double ACCEPT_MARGIN = 1e-4;      // shrink the accept band by this
 constexpr double F_FAIL = 60.0;         // F value used when Phi is not numerically SPD
-constexpr int BRACKET_MAX = 40;
 
 // ---------------------------------------------------------------------------
 // lane-private scratch, interleaved across the warp
@@ -65,12 +73,14 @@ __host__ __device__ inline int pk(int i, int j) { return i * (i + 1) / 2 + j; }
 struct Layout {
     int m;       // padded stencil size (multiple of 4)
     int P;       // m (m + 1) / 2
-    int R2, L, PH, XS, NS, U, ID, Q0, Q1, Q2, T0, GV, HV;
+    int R2, L, PH, XS, NS, U, ID, Q0, Q1, Q2, T0, GV, HV, QB, RV;
     int size;    // doubles per lane
 };
 
-// full = true: the weights kernel's layout (adds the Phi copy, normals and
-// the gradient vectors); the search needs only r^2, L and the vectors.
+// full = true: the weights kernel's layout; full = false: the search's, which
+// adds the Lanczos basis and the Ritz vector kept between evaluations (both
+// hold the Phi copy, normals and gradient vectors: the search computes the
+// weights from its last factorisation).
 __host__ __device__ inline Layout make_layout(int m, bool full) {
     Layout l;
     l.m = m;
@@ -78,6 +88,7 @@ __host__ __device__ inline Layout make_layout(int m, bool full) {
     int o = 0;
     l.R2 = o; o += l.P;
     l.L = o; o += l.P;
+    l.PH = o; o += l.P;
     l.XS = o; o += 3 * m;
     l.U = o; o += m;
     l.ID = o; o += m;
@@ -85,12 +96,13 @@ __host__ __device__ inline Layout make_layout(int m, bool full) {
     l.Q1 = o; o += m;
     l.Q2 = o; o += m;
     l.T0 = o; o += m;
-    l.PH = l.NS = l.GV = l.HV = -1;
-    if (full) {
-        l.PH = o; o += l.P;
-        l.NS = o; o += 3 * m;
-        l.GV = o; o += 3 * m;
-        l.HV = o; o += 3 * m;
+    l.NS = o; o += 3 * m;
+    l.GV = o; o += 3 * m;
+    l.HV = o; o += 3 * m;
+    l.QB = l.RV = -1;
+    if (!full) {
+        l.QB = o; o += LANCZOS_KMAX * m;   // Lanczos basis
+        l.RV = o; o += m;
     }
     l.size = o;
     return l;
@@ -200,16 +212,32 @@ __device__ bool cholesky(const Lane& S, const Layout& ly) {
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     acc[a][b] = (ib + a >= jb + b) ? S[L + pk(ib + a, jb + b)] : 0.0;
-            for (int k = 0; k < jb; ++k) {
+            if (jb > 0) {
+                // software-pipelined: the loads of step k + 1 are in flight
+                // while the 16 FMAs of step k issue
+                const int ra = L + pk(ib, 0), rb = L + pk(jb, 0);
                 double xa[4], yb[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) xa[a] = S[L + pk(ib + a, k)];
+                for (int a = 0; a < 4; ++a) xa[a] = S[ra + a * ib + a * (a + 1) / 2];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) yb[b] = S[L + pk(jb + b, k)];
+                for (int b = 0; b < 4; ++b) yb[b] = S[rb + b * jb + b * (b + 1) / 2];
+                for (int k = 0; k < jb; ++k) {
+                    double xn[4], yn[4];
+                    const int kn = k + 1 < jb ? k + 1 : k;
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < 4; ++a) xn[a] = S[ra + a * ib + a * (a + 1) / 2 + kn];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(-xa[a], yb[b], acc[a][b]);
+                    for (int b = 0; b < 4; ++b) yn[b] = S[rb + b * jb + b * (b + 1) / 2 + kn];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(-xa[a], yb[b], acc[a][b]);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        xa[a] = xn[a];
+                        yb[a] = yn[a];
+                    }
+                }
             }
             if (ib == jb) {
 #pragma unroll
@@ -291,13 +319,22 @@ __device__ void chol_solve(const Lane& S, const Layout& ly, int V) {
             S[V + kb + b] = t[b];
         }
         const int r0 = pk(kb, 0), r1 = pk(kb + 1, 0), r2 = pk(kb + 2, 0), r3 = pk(kb + 3, 0);
-        for (int i = 0; i < kb; ++i) {
-            double v = S[V + i];
-            v = fma(-S[L + r0 + i], t[0], v);
-            v = fma(-S[L + r1 + i], t[1], v);
-            v = fma(-S[L + r2 + i], t[2], v);
-            v = fma(-S[L + r3 + i], t[3], v);
-            S[V + i] = v;
+        // kb is a multiple of 4: four rows per pass keep four independent
+        // FMA chains in flight
+        for (int i = 0; i < kb; i += 4) {
+            double v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = S[V + i + q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r0 + i + q], t[0], v[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r1 + i + q], t[1], v[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r2 + i + q], t[2], v[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r3 + i + q], t[3], v[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) S[V + i + q] = v[q];
         }
     }
 }
@@ -312,12 +349,21 @@ __device__ void chol_mul(const Lane& S, const Layout& ly, int VX, int VY) {
         int r = pk(k, 0);
         for (int i = 0; i <= k; ++i) S[T + i] = fma(S[L + r + i], xk, S[T + i]);
     }
-    // y = L t
-    for (int i = 0; i < m; ++i) {
-        int r = pk(i, 0);
-        double acc = 0.0;
-        for (int k = 0; k <= i; ++k) acc = fma(S[L + r + k], S[T + k], acc);
-        S[VY + i] = acc;
+    // y = L t, four rows at a time (independent accumulators)
+    for (int i = 0; i < m; i += 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        const int r = pk(i, 0);
+        for (int k = 0; k <= i; ++k) {
+            double tk = S[T + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(S[L + r + q * i + q * (q + 1) / 2 + k], tk, acc[q]);
+        }
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+#pragma unroll
+            for (int k = i + 1; k <= i + q; ++k) acc[q] = fma(S[L + r + q * i + q * (q + 1) / 2 + k], S[T + k], acc[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) S[VY + i + q] = acc[q];
     }
 }
 
@@ -336,8 +382,9 @@ __device__ int sturm_below(const float* a, const float* b2, int k, float x) {
     return c;
 }
 
-// largest |eigenvalue| of T (alpha[0..k-1], beta[0..k-2]) in double units
-__device__ double tri_max_abs(const float* a, const float* b2, int k, double scale) {
+// extreme eigenvalues of T (alpha[0..k-1], beta[0..k-2], scaled into
+// [-1, 1]); returns the one of largest magnitude, signed, in double units
+__device__ double tri_extreme(const float* a, const float* b2, int k, double scale) {
     float lo = -1.f, hi = 1.f;
     // top eigenvalue: count(x) < k  <=>  x <= lambda_max
     for (int it = 0; it < 26; ++it) {
@@ -352,7 +399,70 @@ __device__ double tri_max_abs(const float* a, const float* b2, int k, double sca
         if (sturm_below(a, b2, k, mid) >= 1) hi = mid; else lo = mid;
     }
     float bot = 0.5f * (lo + hi);
-    return scale * (double)fmaxf(fabsf(top), fabsf(bot));
+    return scale * (double)(fabsf(top) >= fabsf(bot) ? top : bot);
+}
+
+__device__ double tri_max_abs(const float* a, const float* b2, int k, double scale) {
+    return fabs(tri_extreme(a, b2, k, scale));
+}
+
+// Eigenvector y (unit) of the symmetric tridiagonal T for its eigenvalue
+// theta: two steps of inverse iteration, each a solve with T - theta I by
+// Gaussian elimination with partial pivoting (the factor has two
+// superdiagonals after row exchanges).
+__device__ void tri_eigvec(const double* al, const double* be, int k, double theta, double* y) {
+    double d[LANCZOS_KMAX], du[LANCZOS_KMAX], du2[LANCZOS_KMAX], dl[LANCZOS_KMAX];
+    bool sw[LANCZOS_KMAX];
+    double tmax = 0.0;
+    for (int i = 0; i < k; ++i) tmax = fmax(tmax, fabs(al[i] - theta) + (i < k - 1 ? fabs(be[i]) : 0.0));
+    const double tiny = 1e-30 * (tmax > 0.0 ? tmax : 1.0);
+    for (int i = 0; i < k; ++i) {
+        d[i] = al[i] - theta;
+        du[i] = i < k - 1 ? be[i] : 0.0;
+        dl[i] = i < k - 1 ? be[i] : 0.0;
+        du2[i] = 0.0;
+        sw[i] = false;
+    }
+    for (int i = 0; i < k - 1; ++i) {
+        if (fabs(d[i]) >= fabs(dl[i])) {
+            if (d[i] == 0.0) d[i] = tiny;
+            double f = dl[i] / d[i];
+            dl[i] = f;
+            d[i + 1] -= f * du[i];
+        } else {   // exchange rows i and i + 1
+            double f = d[i] / dl[i];
+            d[i] = dl[i];
+            dl[i] = f;
+            double t = du[i];
+            du[i] = d[i + 1];
+            d[i + 1] = t - f * d[i + 1];
+            if (i < k - 2) {
+                du2[i] = du[i + 1];
+                du[i + 1] = -f * du[i + 1];
+            }
+            sw[i] = true;
+        }
+    }
+    if (d[k - 1] == 0.0) d[k - 1] = tiny;
+    for (int i = 0; i < k; ++i) y[i] = 1.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < k - 1; ++i) {
+            if (sw[i]) {
+                double t = y[i];
+                y[i] = y[i + 1];
+                y[i + 1] = t - dl[i] * y[i + 1];
+            } else {
+                y[i + 1] -= dl[i] * y[i];
+            }
+        }
+        y[k - 1] /= d[k - 1];
+        if (k > 1) y[k - 2] = (y[k - 2] - du[k - 2] * y[k - 1]) / d[k - 2];
+        for (int i = k - 3; i >= 0; --i) y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / d[i];
+        double nrm = 0.0;
+        for (int i = 0; i < k; ++i) nrm = fmax(nrm, fabs(y[i]));
+        double inv = nrm > 0.0 ? 1.0 / nrm : 1.0;
+        for (int i = 0; i < k; ++i) y[i] *= inv;
+    }
 }
 
 // Lanczos with op = A^{-1} (inv = true) or A (inv = false) on augmented
@@ -363,7 +473,7 @@ __device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool i
     const int m = ly.m;
     float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
     double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX];
-    int qp = ly.Q0, q = ly.Q1, w = ly.Q2;
+    int qp = ly.Q0, q_ = ly.Q1, w = ly.Q2;
     // start vector.  For A^{-1}: cos(1.7 i + 0.3) + 0.1 on the n nodes and the
     // border (no preferred direction).  For A: mostly the constant vector,
     // close to the dominant eigenvector when Phi is nearly flat (Phi ~ 1 1^T),
@@ -372,21 +482,21 @@ __device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool i
     for (int i = 0; i < m; ++i) {
         double osc = cos(1.7 * i + 0.3) + 0.1;
         double v = i < n ? (inv ? osc : 1.0 + 0.01 * osc) : 0.0;
-        S[q + i] = v;
+        S[q_ + i] = v;
         S[qp + i] = 0.0;
         nrm2 += v * v;
     }
     double qb = inv ? cos(1.7 * n + 0.3) + 0.1 : 0.1, qpb = 0.0;
     nrm2 += qb * qb;
     double inrm = rsqrt(nrm2);
-    for (int i = 0; i < n; ++i) S[q + i] *= inrm;
+    for (int i = 0; i < n; ++i) S[q_ + i] *= inrm;
     qb *= inrm;
     double beta = 0.0, prev = -1.0, ext = 0.0;
     for (int j = 0; j < LANCZOS_KMAX; ++j) {
         double wb;
         if (inv) {
             // [c; d] = A^{-1} [f; g]: c0 = Phi^{-1} f, d = (1^T c0 - g) / s, c = c0 - d u
-            for (int i = 0; i < m; ++i) S[w + i] = S[q + i];
+            for (int i = 0; i < m; ++i) S[w + i] = S[q_ + i];
             chol_solve(S, ly, w);
             double sum = 0.0;
             for (int i = 0; i < n; ++i) sum += S[w + i];
@@ -394,28 +504,37 @@ __device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool i
             for (int i = 0; i < n; ++i) S[w + i] = fma(-d, S[ly.U + i], S[w + i]);
             wb = d;
         } else {
-            chol_mul(S, ly, q, w);
+            chol_mul(S, ly, q_, w);
             double sum = 0.0;
             for (int i = 0; i < n; ++i) {
-                sum += S[q + i];
+                sum += S[q_ + i];
                 S[w + i] += qb;
             }
             wb = sum;
         }
-        double a = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double v = fma(-beta, S[qp + i], S[w + i]);
-            S[w + i] = v;
-            a = fma(S[q + i], v, a);
+        // four partial sums keep independent FMA chains in flight; entries
+        // n..m-1 of every vector are zero, so the loops run to m
+        double ap[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < m; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double v = fma(-beta, S[qp + i + q], S[w + i + q]);
+                S[w + i + q] = v;
+                ap[q] = fma(S[q_ + i + q], v, ap[q]);
+            }
         }
         wb = fma(-beta, qpb, wb);
-        a = fma(qb, wb, a);
-        double bn = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double v = fma(-a, S[q + i], S[w + i]);
-            S[w + i] = v;
-            bn = fma(v, v, bn);
+        double a = fma(qb, wb, (ap[0] + ap[1]) + (ap[2] + ap[3]));
+        double bp[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < m; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double v = fma(-a, S[q_ + i + q], S[w + i + q]);
+                S[w + i + q] = v;
+                bp[q] = fma(v, v, bp[q]);
+            }
         }
+        double bn = (bp[0] + bp[1]) + (bp[2] + bp[3]);
         wb = fma(-a, qb, wb);
         bn = sqrt(fma(wb, wb, bn));
         alpha_d[j] = a;
@@ -433,184 +552,405 @@ __device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool i
             b2[i] = bb * bb;
         }
         ext = tri_max_abs(al, b2, j + 1, G);
-        if (j + 1 >= LANCZOS_KMIN && fabs(ext - prev) <= rtol * ext) break;
+        // the A run starts next to its dominant eigenvector: two steps can settle
+        if (j + 1 >= (inv ? LANCZOS_KMIN : 2) && fabs(ext - prev) <= rtol * ext) break;
         if (bn <= 1e-14 * fabs(a)) break;
         prev = ext;
         beta = bn;
         double ib = 1.0 / bn;
         int t = qp;
-        qp = q;
-        q = w;
+        qp = q_;
+        q_ = w;
         w = t;
         qpb = qb;
-        for (int i = 0; i < n; ++i) S[q + i] *= ib;
+        for (int i = 0; i < n; ++i) S[q_ + i] *= ib;
         qb = wb * ib;
     }
     return ext;
 }
 
-// kappa_2(A(eps_s)); +inf when Phi is not numerically positive definite.
-__device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel, double eps_s,
-                             double rtol) {
-    assemble_phi(S, ly, n, kernel, eps_s, ly.L, -1);
+// splitmix64 (Steele, Lea, Flood 2014) mapped to [-1, 1): the pseudo-random
+// start vector of the A^{-1} Lanczos run, seeded per stencil, so that no
+// stencil's symmetry can leave it (nearly) orthogonal to the eigenvector of
+// lambda_min, as a fixed smooth start vector can be.
+__device__ inline double unit_hash(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Lanczos with A^{-1} keeping its basis (regions QB + j m, borders in
+// qbord[]): returns the signed Ritz value theta of largest magnitude and
+// writes the unit Ritz vector (m entries, border in *vb) to region RV.
+// Starts from RV when warm (the previous evaluation's Ritz vector), else
+// from the stencil's pseudo-random vector.
+__device__ double lanczos_inv_ritz(const Lane& S, const Layout& ly, int n, double s, double rtol, bool warm,
+                                   double* vb, uint64_t seed) {
+    const int m = ly.m, w = ly.Q2;
+    float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
+    double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX], qbord[LANCZOS_KMAX + 1];
+    double nrm2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double v = i < n ? (warm ? S[ly.RV + i] : unit_hash(seed * 131u + i)) : 0.0;
+        S[ly.QB + i] = v;
+        nrm2 += v * v;
+    }
+    double qb = warm ? *vb : unit_hash(seed * 131u + n);
+    nrm2 += qb * qb;
+    double inrm = rsqrt(nrm2);
+    for (int i = 0; i < n; ++i) S[ly.QB + i] *= inrm;
+    qbord[0] = qb * inrm;
+    const int kmin = warm ? 2 : LANCZOS_KMIN;
+    double beta = 0.0, prev = -1.0, ext = 0.0;
+    int k = 0;
+    for (int j = 0; j < LANCZOS_KMAX; ++j) {
+        const int qj = ly.QB + j * m, qp = ly.QB + (j - 1) * m;
+        // [c; d] = A^{-1} [f; g]: c0 = Phi^{-1} f, d = (1^T c0 - g) / s, c = c0 - d u
+        for (int i = 0; i < m; ++i) S[w + i] = S[qj + i];
+        chol_solve(S, ly, w);
+        double sp[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < m; i += 4)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sp[q] += S[w + i + q];
+        double dd = ((sp[0] + sp[1]) + (sp[2] + sp[3]) - qbord[j]) / s;
+        for (int i = 0; i < n; ++i) S[w + i] = fma(-dd, S[ly.U + i], S[w + i]);
+        double wb = dd;
+        double ap[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < m; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double v = S[w + i + q];
+                if (j > 0) v = fma(-beta, S[qp + i + q], v);
+                S[w + i + q] = v;
+                ap[q] = fma(S[qj + i + q], v, ap[q]);
+            }
+        }
+        if (j > 0) wb = fma(-beta, qbord[j - 1], wb);
+        double a = fma(qbord[j], wb, (ap[0] + ap[1]) + (ap[2] + ap[3]));
+        double bp[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < m; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double v = fma(-a, S[qj + i + q], S[w + i + q]);
+                S[w + i + q] = v;
+                bp[q] = fma(v, v, bp[q]);
+            }
+        }
+        wb = fma(-a, qbord[j], wb);
+        double bn = sqrt(fma(wb, wb, (bp[0] + bp[1]) + (bp[2] + bp[3])));
+        alpha_d[j] = a;
+        beta_d[j] = bn;
+        k = j + 1;
+        double G = 0.0;
+        for (int i = 0; i <= j; ++i) {
+            double r = fabs(alpha_d[i]) + (i < j ? beta_d[i] : 0.0) + (i > 0 ? beta_d[i - 1] : 0.0);
+            G = fmax(G, r);
+        }
+        double ig = 1.0 / G;
+        for (int i = 0; i <= j; ++i) {
+            al[i] = (float)(alpha_d[i] * ig);
+            float bb = (float)(beta_d[i] * ig);
+            b2[i] = bb * bb;
+        }
+        ext = tri_extreme(al, b2, j + 1, G);
+        if (j + 1 >= kmin && fabs(fabs(ext) - prev) <= rtol * fabs(ext)) break;
+        if (bn <= 1e-14 * fabs(a) || j + 1 == LANCZOS_KMAX) break;
+        prev = fabs(ext);
+        beta = bn;
+        const double ib = 1.0 / bn;
+        const int qn = ly.QB + (j + 1) * m;
+        for (int i = 0; i < m; ++i) S[qn + i] = S[w + i] * ib;
+        qbord[j + 1] = wb * ib;
+    }
+    // Ritz vector  v = sum_j y_j q_j
+    double y[LANCZOS_KMAX];
+    tri_eigvec(alpha_d, beta_d, k, ext, y);
+    double vbr = 0.0, nv = 0.0;
+    for (int j = 0; j < k; ++j) vbr = fma(y[j], qbord[j], vbr);
+    for (int i = 0; i < m; ++i) {
+        double v = 0.0;
+        for (int j = 0; j < k; ++j) v = fma(y[j], S[ly.QB + j * m + i], v);
+        S[ly.RV + i] = v;
+        nv = fma(v, v, nv);
+    }
+    nv = fma(vbr, vbr, nv);
+    double inv = nv > 0.0 ? rsqrt(nv) : 0.0;
+    for (int i = 0; i < m; ++i) S[ly.RV + i] *= inv;
+    *vb = vbr * inv;
+    return ext;
+}
+
+// d lambda / d eps_s = v^T (dA/d eps_s) v for the unit eigenvector v in RV
+// (Hellmann-Feynman; the border of A does not depend on eps).
+__device__ double eig_derivative(const Lane& S, const Layout& ly, int n, int kernel, double eps_s) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 1; i < n; ++i) {
+        const int base = pk(i, 0);
+        const double vi = S[ly.RV + i];
+        double row[4] = {0.0, 0.0, 0.0, 0.0};
+        int j = 0;
+        for (; j + 4 <= i; j += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double ph = S[ly.PH + base + j + q];
+                double g = kernel == RBFFD_GAUSSIAN ? 2.0 * ph : ph * ph * ph;   // -dphi/(eps r^2)
+                row[q] = fma(g * S[ly.R2 + base + j + q], S[ly.RV + j + q], row[q]);
+            }
+        }
+        for (; j < i; ++j) {
+            double ph = S[ly.PH + base + j];
+            double g = kernel == RBFFD_GAUSSIAN ? 2.0 * ph : ph * ph * ph;
+            row[0] = fma(g * S[ly.R2 + base + j], S[ly.RV + j], row[0]);
+        }
+        acc[i & 3] = fma(vi, (row[0] + row[1]) + (row[2] + row[3]), acc[i & 3]);
+    }
+    // dPhi_ij/d eps = -eps r_ij^2 phi^3 (IMQ) or -2 eps r_ij^2 phi (Gaussian);
+    // the double sum over i != j is twice the lower-triangle sum
+    return -2.0 * eps_s * ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+}
+
+// kappa_2(A(eps_s)) (+inf when Phi is not numerically positive definite)
+// and dF/dx, F = ln(kappa / kappa_T), x = ln eps_s: the derivative of
+// -ln|lambda_min| by Hellmann-Feynman with the Ritz vector of the A^{-1}
+// Lanczos run (d ln lambda_max / dx is ~1% of it on these stencils and is
+// left out: Newton then still converges, linearly at rate ~0.01).  The Ritz
+// vector stays in RV as the next evaluation's start vector.
+__device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel, double eps_s, bool warm,
+                             double* vb, double* theta_out, double* schur, uint64_t seed) {
+    double* dF = theta_out;
+    *dF = NAN;
+    *schur = 0.0;
+    assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH);
     if (!cholesky(S, ly)) return INFINITY;
     for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
     chol_solve(S, ly, ly.U);
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += S[ly.U + i];
     if (!(s > 0.0)) return INFINITY;
-    double tinv = lanczos_extreme(S, ly, n, true, s, rtol);
-    double lmax = lanczos_extreme(S, ly, n, false, s, rtol);
-    double k = lmax * tinv;
-    return isfinite(k) ? k : INFINITY;
+    *schur = s;
+    double theta = lanczos_inv_ritz(S, ly, n, s, LANCZOS_RTOL, warm, vb, seed);
+    double lmax = lanczos_extreme(S, ly, n, false, s, LANCZOS_RTOL);
+    double k = lmax * fabs(theta);
+    if (!isfinite(k)) return INFINITY;
+    *dF = theta;   // the caller turns it into dF/dx with kappa_slope() when needed
+    return k;
+}
+
+// dF/dx from the Ritz vector left in RV by eval_kappa (theta = its Ritz value)
+__device__ inline double kappa_slope(const Lane& S, const Layout& ly, int n, int kernel, double eps_s,
+                                     double theta) {
+    return -eps_s * theta * eig_derivative(S, ly, n, kernel, eps_s);
 }
 
 // ---------------------------------------------------------------------------
-// per-lane root finder: secant bracketing then Brent-Dekker in x = ln eps_s
+// per-lane root finder: safeguarded Newton in x = ln eps_s
 // ---------------------------------------------------------------------------
-enum { PH_FIRST = 0, PH_BRACKET = 1, PH_BRENT = 2, PH_DONE = 3 };
+enum { PH_FIRST = 0, PH_NEWTON = 1, PH_DONE = 3 };
 
 struct Search {
-    double x_next;               // point to evaluate next
-    double x0, f0;               // previous point while bracketing
-    double a, b, c, fa, fb, fc, d, e;   // Brent state (b: best)
-    double ka, kb, kc;                  // kappa at a, b, c
-    double xtol;
-    double k0;
-    int phase, evals, nbr;
+    double x_next;        // point to evaluate next
+    double lo, hi;        // bracket of the root: F(lo) > 0 > F(hi) (F decreases)
+    double x_ret, k_ret;  // result (eps_s = exp(x_ret)) and kappa reported for it
+    double dx_prev;
+    double f_prev;        // |F| at the previous iterate
+    int phase, evals;
     int status;
 };
 
 __device__ inline double clampd(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
 
-// Brent-Dekker step after fb is known for b.  Returns true when converged.
-__device__ bool brent_step(Search& s) {
-    if ((s.fb > 0.0 && s.fc > 0.0) || (s.fb < 0.0 && s.fc < 0.0)) {
-        s.c = s.a;
-        s.fc = s.fa;
-        s.kc = s.ka;
-        s.d = s.e = s.b - s.a;
-    }
-    if (fabs(s.fc) < fabs(s.fb)) {
-        s.a = s.b; s.b = s.c; s.c = s.a;
-        s.fa = s.fb; s.fb = s.fc; s.fc = s.fa;
-        s.ka = s.kb; s.kb = s.kc; s.kc = s.ka;
-    }
-    const double u = 2.220446049250313e-16;
-    double tol1 = 2.0 * u * fabs(s.b) + 0.5 * s.xtol;
-    double mid = 0.5 * (s.c - s.b);
-    if (fabs(mid) <= tol1 || s.fb == 0.0) return true;
-    if (fabs(s.e) >= tol1 && fabs(s.fa) > fabs(s.fb)) {
-        double p, q, r;
-        double sr = s.fb / s.fa;
-        if (s.a == s.c) {
-            p = 2.0 * mid * sr;
-            q = 1.0 - sr;
-        } else {
-            q = s.fa / s.fc;
-            r = s.fb / s.fc;
-            p = sr * (2.0 * mid * q * (q - r) - (s.b - s.a) * (r - 1.0));
-            q = (q - 1.0) * (r - 1.0) * (sr - 1.0);
-        }
-        if (p > 0.0) q = -q; else p = -p;
-        if (2.0 * p < fmin(3.0 * mid * q - fabs(tol1 * q), fabs(s.e * q))) {
-            s.e = s.d;
-            s.d = p / q;
-        } else {
-            s.d = mid;
-            s.e = s.d;
-        }
-    } else {
-        s.d = mid;
-        s.e = s.d;
-    }
-    s.a = s.b;
-    s.fa = s.fb;
-    s.ka = s.kb;
-    s.b += fabs(s.d) > tol1 ? s.d : copysign(tol1, mid);
-    s.x_next = s.b;
-    return false;
-}
-
-__device__ void enter_brent(Search& s, double xl, double fl, double kl, double xr, double fr,
-                            double kr, double tol_s) {
-    s.a = xl; s.fa = fl; s.ka = kl;
-    s.b = xr; s.fb = fr; s.kb = kr;
-    s.c = s.a; s.fc = s.fa; s.kc = s.ka;
-    s.d = s.e = s.b - s.a;
-    s.xtol = tol_s / exp(fmax(xl, xr));
-    s.phase = PH_BRENT;
-}
-
-// dF/dx near the root, F = ln(kappa / kappa_T), x = ln(eps r_s): about
-// -(11 + n / 10) for both kernels on quasi-uniform surface stencils
-// (measured); only used to aim the first secant step.
+// dF/dx near the root, about -(11 + n / 10) on quasi-uniform surface
+// stencils (measured); used when the computed derivative is unusable.
 __device__ inline double slope_model(int n) { return -(11.0 + 0.1 * n); }
 
-// Consume F(x_next) = f (kappa k).  Sets phase PH_DONE when finished.
-__device__ void search_update(Search& s, double f, double k, double tol_s, int max_evals,
+__device__ inline void finish(Search& s, double x, double k, int status) {
+    s.x_ret = x;
+    s.k_ret = k;
+    s.status = status;
+    s.phase = PH_DONE;
+}
+
+// Consume F(x_next) = f with derivative d and kappa k.
+//  * learned first guess: accepted when kappa is inside the band;
+//  * Newton step dx = -f/d (slope model if d is unusable), clamped to +-3,
+//    replaced by bisection of the bracket when it would leave it;
+//  * stop when |dx| < xtol/2, when the bracket is narrower than xtol, or
+//    when the steps stop shrinking at the float64 noise floor of kappa
+//    (|dx| < xtol and at least 0.9 of the previous step); every stop returns
+//    the evaluated x, within xtol of the root (the oracle's Brent guarantee).
+__device__ void search_update(Search& s, double f, double d, double k, double tol_s, int max_evals,
                               double acc_lo, double acc_hi, bool learned, int n) {
     s.evals++;
-    double x = s.x_next;
-    if (s.phase == PH_FIRST) {
-        if (learned && k >= acc_lo * (1.0 + ACCEPT_MARGIN) && k <= acc_hi * (1.0 - ACCEPT_MARGIN)) {
-            s.b = x; s.fb = f; s.kb = k;
-            s.status = RBFFD_STENCIL_ACCEPTED_PREDICTION;
-            s.phase = PH_DONE;
-            return;
-        }
-        s.x0 = x; s.f0 = f; s.k0 = k;
-        s.x_next = x + clampd(-f / slope_model(n), -3.0, 3.0);
-        if (f == 0.0) {
-            s.b = x; s.kb = k; s.phase = PH_DONE;
-            return;
-        }
-        s.phase = PH_BRACKET;
-        s.nbr = 0;
+    const double x = s.x_next;
+    if (s.phase == PH_FIRST && learned && k >= acc_lo && k <= acc_hi) {
+        finish(s, x, k, RBFFD_STENCIL_ACCEPTED_PREDICTION);
         return;
     }
-    if (s.phase == PH_BRACKET) {
-        if ((f > 0.0) != (s.f0 > 0.0) || f == 0.0) {
-            if (f == 0.0) {
-                s.b = x; s.kb = k; s.phase = PH_DONE;
-                return;
-            }
-            // Brent from the bracket, with b at the newest point
-            enter_brent(s, s.x0, s.f0, s.k0, x, f, k, tol_s);
-            if (brent_step(s)) s.phase = PH_DONE;
-            return;
-        }
-        if (++s.nbr >= BRACKET_MAX || s.evals >= max_evals) {
-            s.status = RBFFD_STENCIL_NO_BRACKET;
-            s.b = x; s.kb = k; s.phase = PH_DONE;
-            return;
-        }
-        double slope = (f - s.f0) / (x - s.x0);
-        if (!(slope < -0.5) || !isfinite(slope)) slope = slope_model(n);
-        double step = clampd(-f / slope, -3.0, 3.0);
-        double dir = f > 0.0 ? 1.0 : -1.0;   // F decreases with x
-        if (step * dir < 0.05) step = 0.05 * dir;
-        s.x0 = x; s.f0 = f; s.k0 = k;
-        s.x_next = x + step;
+    if (f == 0.0) {
+        finish(s, x, k, RBFFD_STENCIL_OK);
         return;
     }
-    // Brent
-    s.fb = f;
-    s.kb = k;
+    if (f > 0.0) s.lo = fmax(s.lo, x); else s.hi = fmin(s.hi, x);
+    const double xtol = tol_s / exp(x);
+    // the Hellmann-Feynman slope is trusted only within a factor 5 of the
+    // slope model (a Ritz vector from a clustered pair can be poor)
+    const double sm = slope_model(n);
+    const bool usable = isfinite(d) && isfinite(f) && f != F_FAIL && d <= 0.2 * sm && d >= 5.0 * sm;
+    double dx = clampd(-f / (usable ? d : sm), -3.0, 3.0);
+    double xn = x + dx;
+    const bool bracketed = isfinite(s.lo) && isfinite(s.hi);
+    // safeguard: bisect when the Newton point leaves the bracket, or when the
+    // last Newton step did not halve |F| (the bracket then still shrinks
+    // geometrically, whatever the quality of the slope)
+    const bool slow = s.phase == PH_NEWTON && fabs(f) > 0.5 * s.f_prev;
+    if (bracketed && (!(xn > s.lo && xn < s.hi) || slow)) {
+        xn = 0.5 * (s.lo + s.hi);
+        dx = xn - x;
+    }
+    // every stop returns the evaluated x (its factorisation is still in
+    // scratch for the weights): x is within |dx| (1 + O(dx)) of the root
+    if (usable && fabs(dx) < 0.5 * xtol) {
+        finish(s, x, k, RBFFD_STENCIL_OK);
+        return;
+    }
+    if (bracketed && s.hi - s.lo < xtol) {
+        finish(s, x, k, RBFFD_STENCIL_OK);
+        return;
+    }
+    // float64 noise floor of kappa: tiny steps that no longer shrink (a
+    // linearly converging Newton, e.g. with a slope off by 2x, shrinks its
+    // steps by a constant factor and does not stop here; when it is slow the
+    // halving test above bisects instead)
+    if (s.phase == PH_NEWTON && usable && fabs(dx) < xtol && fabs(dx) >= 0.9 * fabs(s.dx_prev)) {
+        finish(s, x, k, RBFFD_STENCIL_OK);
+        return;
+    }
     if (s.evals >= max_evals) {
-        s.status = RBFFD_STENCIL_NO_CONVERGENCE;
-        s.phase = PH_DONE;
+        finish(s, x, k, bracketed ? RBFFD_STENCIL_NO_CONVERGENCE : RBFFD_STENCIL_NO_BRACKET);
         return;
     }
-    if (brent_step(s)) s.phase = PH_DONE;
+    s.dx_prev = dx;
+    s.f_prev = fabs(f);
+    s.x_next = xn;
+    s.phase = PH_NEWTON;
 }
 
 __device__ inline double F_of(double k, double kT) {
     return isfinite(k) ? log(k / kT) : F_FAIL;
 }
 
+// [c; d] = A^{-1} [f; 0] in place on region V (first n entries)
+__device__ void aug_solve0(const Lane& S, const Layout& ly, int n, int V, double s) {
+    chol_solve(S, ly, V);
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) sum += S[V + i];
+    double d = sum / s;
+    for (int i = 0; i < n; ++i) S[V + i] = fma(-d, S[ly.U + i], S[V + i]);
+}
+
+// Three right-hand sides (regions V, V + m, V + 2m) solved together with
+// Phi = L L^T: every element of L is loaded once for three FMAs.
+__device__ void chol_solve_x3(const Lane& S, const Layout& ly, int V) {
+    const int m = ly.m, L = ly.L;
+    for (int i = 0; i < m; ++i) {   // forward
+        double t0 = S[V + i], t1 = S[V + m + i], t2 = S[V + 2 * m + i];
+        const int r = pk(i, 0);
+        for (int k = 0; k < i; ++k) {
+            double l = S[L + r + k];
+            t0 = fma(-l, S[V + k], t0);
+            t1 = fma(-l, S[V + m + k], t1);
+            t2 = fma(-l, S[V + 2 * m + k], t2);
+        }
+        double id = S[ly.ID + i];
+        S[V + i] = t0 * id;
+        S[V + m + i] = t1 * id;
+        S[V + 2 * m + i] = t2 * id;
+    }
+    for (int k = m - 1; k >= 0; --k) {   // backward, column-oriented
+        double id = S[ly.ID + k];
+        double x0 = S[V + k] * id, x1 = S[V + m + k] * id, x2 = S[V + 2 * m + k] * id;
+        S[V + k] = x0;
+        S[V + m + k] = x1;
+        S[V + 2 * m + k] = x2;
+        const int r = pk(k, 0);
+        for (int i = 0; i < k; ++i) {
+            double l = S[L + r + i];
+            S[V + i] = fma(-l, x0, S[V + i]);
+            S[V + m + i] = fma(-l, x1, S[V + m + i]);
+            S[V + 2 * m + i] = fma(-l, x2, S[V + 2 * m + i]);
+        }
+    }
+}
+
+__device__ void aug_solve0_x3(const Lane& S, const Layout& ly, int n, int V, double s) {
+    const int m = ly.m;
+    chol_solve_x3(S, ly, V);
+    for (int d = 0; d < 3; ++d) {
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) sum += S[V + d * m + i];
+        double dd = sum / s;
+        for (int i = 0; i < n; ++i) S[V + d * m + i] = fma(-dd, S[ly.U + i], S[V + d * m + i]);
+    }
+}
+
+// First row of L_P from a factorised Phi(eps_s) (regions L, ID, U = Phi^{-1} 1,
+// Schur complement s, the Phi copy PH, scaled coordinates XS and normals NS):
+//   g_d = (A^{-1} [B^d row 0; 0])[:n],  h_i = P_i g_i,
+//   v_j = sum_i psi_ij (x_i - x_j) . h_i,  w = (A^{-1} [v; 0])[:n].
+// Leaves the scaled weights (times r_s^2) in region Q0.
+__device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int kernel, double eps_s, double s) {
+    const int XS = ly.XS, m = ly.m;
+    const double e2 = eps_s * eps_s;
+    // centre projector P_0 = I - n_0 n_0^T; rhs_d,j = psi(r_0j) [P_0 (x_0 - x_j)]_d
+    double n0x = S[ly.NS], n0y = S[ly.NS + m], n0z = S[ly.NS + 2 * m];
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < m; ++i) S[ly.GV + d * m + i] = 0.0;
+    for (int j = 1; j < n; ++j) {
+        double ph = S[ly.PH + pk(j, 0)];
+        double ps = psi_from_phi(kernel, e2, ph);
+        double dx = -S[XS + j], dy = -S[XS + m + j], dz = -S[XS + 2 * m + j];   // x_0 - x_j
+        double nd = n0x * dx + n0y * dy + n0z * dz;
+        S[ly.GV + j] = ps * (dx - n0x * nd);
+        S[ly.GV + m + j] = ps * (dy - n0y * nd);
+        S[ly.GV + 2 * m + j] = ps * (dz - n0z * nd);
+    }
+    aug_solve0_x3(S, ly, n, ly.GV, s);
+    // h_i = P_i g_i
+    for (int i = 0; i < n; ++i) {
+        double gx = S[ly.GV + i], gy = S[ly.GV + m + i], gz = S[ly.GV + 2 * m + i];
+        double nx = S[ly.NS + i], ny = S[ly.NS + m + i], nz = S[ly.NS + 2 * m + i];
+        double nd = nx * gx + ny * gy + nz * gz;
+        S[ly.HV + i] = gx - nx * nd;
+        S[ly.HV + m + i] = gy - ny * nd;
+        S[ly.HV + 2 * m + i] = gz - nz * nd;
+    }
+    const int V = ly.Q0;
+    for (int i = 0; i < m; ++i) S[V + i] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double xi = S[XS + i], yi = S[XS + m + i], zi = S[XS + 2 * m + i];
+        double hx = S[ly.HV + i], hy = S[ly.HV + m + i], hz = S[ly.HV + 2 * m + i];
+        double vi = 0.0;
+        int base = pk(i, 0);
+        for (int j = 0; j < i; ++j) {
+            double ps = psi_from_phi(kernel, e2, S[ly.PH + base + j]);
+            double dx = xi - S[XS + j], dy = yi - S[XS + m + j], dz = zi - S[XS + 2 * m + j];
+            double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
+            // pair (i, j): v_j += psi (x_i - x_j) . h_i ; v_i += psi (x_j - x_i) . h_j
+            S[V + j] = fma(ps, dx * hx + dy * hy + dz * hz, S[V + j]);
+            vi = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi);
+        }
+        S[V + i] += vi;
+    }
+    aug_solve0(S, ly, n, V, s);
+}
+
 struct SearchArgs {
     const double* X;
+    const double* NR;
+    double* w64;
+    float* w32;
     const int32_t* idx;
     const int32_t* row_node;
     GroupInfo gi;
@@ -641,6 +981,7 @@ __global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
     geo.rs = 1.0;
     double tol_s = 0.0;
     bool learned = false;
+    double vborder = 0.0;     // border entry of the Ritz vector in RV
     while (true) {
         if (!have) {
             unsigned long long t = atomicAdd(&A.counters[g], 1ull);
@@ -649,12 +990,15 @@ __global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
                 have = true;
                 lr = (int64_t)t;
                 r = A.gi.row_begin[g] + lr;
-                geo = load_geometry(S, ly, n, A.idx, A.gi.ell_off[g], A.gi.npad[g], lr, A.X, nullptr,
-                                    false);
+                geo = load_geometry(S, ly, n, A.idx, A.gi.ell_off[g], A.gi.npad[g], lr, A.X, A.NR, true);
                 tol_s = A.tol * geo.rs;
                 st.phase = PH_FIRST;
                 st.evals = 0;
                 st.status = RBFFD_STENCIL_OK;
+                st.lo = -INFINITY;
+                st.hi = INFINITY;
+                st.dx_prev = INFINITY;
+                st.f_prev = INFINITY;
                 float gs = A.guess_rows ? A.guess_rows[r] : NAN;
                 learned = isfinite(gs);
                 st.x_next = learned ? (double)gs : log(1.0 / geo.mean_d);
@@ -667,15 +1011,38 @@ __global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
             continue;
         }
         if (have) {
-            double k = eval_kappa(S, ly, n, A.kernel, exp(st.x_next), LANCZOS_RTOL);
-            search_update(st, F_of(k, A.kT), k, tol_s, A.max_evals, A.acc_lo * A.kT, A.acc_hi * A.kT,
-                          learned, n);
+            double dF, schur;
+            // every evaluation starts its A^{-1} Lanczos run cold: a start from
+            // the previous Ritz vector can stay on that eigenvalue's branch
+            // when the two smallest eigenvalues cross, and then misjudge kappa
+            const double eps_s = exp(st.x_next);
+            const double acc_lo = A.acc_lo * A.kT * (1.0 + ACCEPT_MARGIN);
+            const double acc_hi = A.acc_hi * A.kT * (1.0 - ACCEPT_MARGIN);
+            double theta;
+            double k = eval_kappa(S, ly, n, A.kernel, eps_s, false, &vborder, &theta, &schur,
+                                  (uint64_t)A.row_node[r]);
+            // the slope is needed unless a learned guess is accepted now
+            const bool accept_now = learned && st.phase == PH_FIRST && k >= acc_lo && k <= acc_hi;
+            dF = (isfinite(k) && !accept_now) ? kappa_slope(S, ly, n, A.kernel, eps_s, theta) : NAN;
+            search_update(st, F_of(k, A.kT), dF, k, tol_s, A.max_evals, acc_lo, acc_hi, learned, n);
             if (st.phase == PH_DONE) {
-                int node = A.row_node[r];
-                A.eps[node] = exp(st.b) / geo.rs;
-                A.kappa[node] = st.kb;
+                // the search stopped at its last evaluated point, whose
+                // factorisation is still in scratch: the weights follow
+                const int node = A.row_node[r];
+                const int npad = A.gi.npad[g];
+                const int64_t off = A.gi.ell_off[g];
+                const bool valid = isfinite(st.k_ret) && schur > 0.0;
+                if (valid) first_row_weights(S, ly, n, A.kernel, exp(st.x_ret), schur);
+                const double inv_rs2 = 1.0 / (geo.rs * geo.rs);
+                for (int j = 0; j < npad; ++j) {
+                    double w = (valid && j < n) ? S[ly.Q0 + j] * inv_rs2 : 0.0;
+                    A.w64[ell_elem(off, npad, lr, j)] = w;
+                    A.w32[ell_elem(off, npad, lr, j)] = (float)w;
+                }
+                A.eps[node] = exp(st.x_ret) / geo.rs;
+                A.kappa[node] = st.k_ret;
                 A.evals[node] = st.evals;
-                A.status[node] = st.status;
+                A.status[node] = valid ? st.status : RBFFD_STENCIL_SINGULAR;
                 have = false;
             }
         }
@@ -701,15 +1068,6 @@ struct WeightArgs {
     int* nfail;
 };
 
-// [c; d] = A^{-1} [f; 0] in place on region V (first n entries)
-__device__ void aug_solve0(const Lane& S, const Layout& ly, int n, int V, double s) {
-    chol_solve(S, ly, V);
-    double sum = 0.0;
-    for (int i = 0; i < n; ++i) sum += S[V + i];
-    double d = sum / s;
-    for (int i = 0; i < n; ++i) S[V + i] = fma(-d, S[ly.U + i], S[V + i]);
-}
-
 __global__ void __launch_bounds__(128) weights_kernel(WeightArgs A) {
     const int lane_id = threadIdx.x & 31;
     const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -724,7 +1082,6 @@ __global__ void __launch_bounds__(128) weights_kernel(WeightArgs A) {
         Geo geo = load_geometry(S, ly, n, A.idx, off, npad, lr, A.X, A.NR, true);
         int node = A.row_node[r];
         double eps_s = A.eps_node[node] * geo.rs;
-        double e2 = eps_s * eps_s;
         assemble_phi(S, ly, n, A.kernel, eps_s, ly.L, ly.PH);
         bool ok = cholesky(S, ly) && isfinite(eps_s) && eps_s > 0.0;
         double s = 0.0;
@@ -743,49 +1100,8 @@ __global__ void __launch_bounds__(128) weights_kernel(WeightArgs A) {
             }
             continue;
         }
-        const int XS = ly.XS, m = ly.m;
-        // centre projector P_0 = I - n_0 n_0^T; rhs_d,j = psi(r_0j) [P_0 (x_0 - x_j)]_d
-        double n0x = S[ly.NS], n0y = S[ly.NS + m], n0z = S[ly.NS + 2 * m];
-        for (int d = 0; d < 3; ++d)
-            for (int i = 0; i < m; ++i) S[ly.GV + d * m + i] = 0.0;
-        for (int j = 1; j < n; ++j) {
-            double ph = S[ly.PH + pk(j, 0)];
-            double ps = psi_from_phi(A.kernel, e2, ph);
-            double dx = -S[XS + j], dy = -S[XS + m + j], dz = -S[XS + 2 * m + j];   // x_0 - x_j
-            double nd = n0x * dx + n0y * dy + n0z * dz;
-            S[ly.GV + j] = ps * (dx - n0x * nd);
-            S[ly.GV + m + j] = ps * (dy - n0y * nd);
-            S[ly.GV + 2 * m + j] = ps * (dz - n0z * nd);
-        }
-        for (int d = 0; d < 3; ++d) aug_solve0(S, ly, n, ly.GV + d * m, s);
-        // h_i = P_i g_i
-        for (int i = 0; i < n; ++i) {
-            double gx = S[ly.GV + i], gy = S[ly.GV + m + i], gz = S[ly.GV + 2 * m + i];
-            double nx = S[ly.NS + i], ny = S[ly.NS + m + i], nz = S[ly.NS + 2 * m + i];
-            double nd = nx * gx + ny * gy + nz * gz;
-            S[ly.HV + i] = gx - nx * nd;
-            S[ly.HV + m + i] = gy - ny * nd;
-            S[ly.HV + 2 * m + i] = gz - nz * nd;
-        }
-        // v_j = sum_i psi_ij (x_i - x_j) . h_i   (v in region T0... use Q0)
+        first_row_weights(S, ly, n, A.kernel, eps_s, s);
         const int V = ly.Q0;
-        for (int i = 0; i < m; ++i) S[V + i] = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double xi = S[XS + i], yi = S[XS + m + i], zi = S[XS + 2 * m + i];
-            double hx = S[ly.HV + i], hy = S[ly.HV + m + i], hz = S[ly.HV + 2 * m + i];
-            double vi = 0.0;
-            int base = pk(i, 0);
-            for (int j = 0; j < i; ++j) {
-                double ps = psi_from_phi(A.kernel, e2, S[ly.PH + base + j]);
-                double dx = xi - S[XS + j], dy = yi - S[XS + m + j], dz = zi - S[XS + 2 * m + j];
-                double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
-                // pair (i, j): v_j += psi (x_i - x_j) . h_i ; v_i += psi (x_j - x_i) . h_j
-                S[V + j] = fma(ps, dx * hx + dy * hy + dz * hz, S[V + j]);
-                vi = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi);
-            }
-            S[V + i] += vi;
-        }
-        aug_solve0(S, ly, n, V, s);
         double inv_rs2 = 1.0 / (geo.rs * geo.rs);
         for (int j = 0; j < npad; ++j) {
             double w = j < n ? S[V + j] * inv_rs2 : 0.0;
@@ -813,7 +1129,6 @@ LaunchShape launch_shape(const rbffd_build_opts& o, int64_t rows) {
 
 rbffd_status build_search(rbffd_op* op, const double* nodes, const double* normals,
                           const rbffd_build_opts& o, const float* guess_rows, cudaStream_t st) {
-    (void)normals;
     const GroupInfo& gi = op->gi;
     int mmax = 0;
     for (int g = 0; g < gi.ngroups; ++g) mmax = std::max(mmax, gi.npad[g]);
@@ -828,6 +1143,9 @@ rbffd_status build_search(rbffd_op* op, const double* nodes, const double* norma
     RBFFD_CUDA_TRY(cudaMemsetAsync(ctr, 0, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
     SearchArgs A;
     A.X = nodes;
+    A.NR = normals;
+    A.w64 = op->w64;
+    A.w32 = op->w32;
     A.idx = op->idx;
     A.row_node = op->row_node;
     A.gi = gi;

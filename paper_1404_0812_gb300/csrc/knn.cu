@@ -67,6 +67,7 @@ struct Grid {
     double lo[3];
     double h, inv_h;
     int G[3];
+    double delta;   // bound on the float32 error of one coordinate difference
 };
 
 __device__ inline int cell_coord(double x, double lo, double inv_h, int G) {
@@ -134,7 +135,7 @@ rbffd_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStre
 __global__ void scatter_nodes(const double* __restrict__ X, int64_t N,
                               const int32_t* __restrict__ cell, const int32_t* __restrict__ start,
                               int32_t* __restrict__ cursor, int32_t* __restrict__ sidx,
-                              double* __restrict__ sx) {
+                              double* __restrict__ sx, float4* __restrict__ sxf) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     int c = cell[i];
@@ -143,6 +144,12 @@ __global__ void scatter_nodes(const double* __restrict__ X, int64_t N,
     sx[3 * (int64_t)p] = X[3 * i];
     sx[3 * (int64_t)p + 1] = X[3 * i + 1];
     sx[3 * (int64_t)p + 2] = X[3 * i + 2];
+    sxf[p] = make_float4((float)X[3 * i], (float)X[3 * i + 1], (float)X[3 * i + 2], 0.f);
+}
+
+__global__ void invert_rows(const int32_t* __restrict__ row_node, int64_t N, int32_t* __restrict__ node_row) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < N) node_row[row_node[r]] = (int32_t)r;
 }
 
 // Bit-reproducible squared distance: no contraction into FMA.
@@ -156,19 +163,24 @@ __device__ __forceinline__ bool key_less(double da, int ia, double db, int ib) {
     return da < db || (da == db && ia < ib);
 }
 
+// One thread per query, queries taken in cell-sorted order so that the 32
+// queries of a warp share nearby cells.
 __global__ void __launch_bounds__(128)
-knn_query(const double* __restrict__ X, const int32_t* __restrict__ row_node, int64_t nrows_total,
+knn_query(const double* __restrict__ X, const int32_t* __restrict__ node_row, int64_t nrows_total,
           GroupInfo gi, Grid g, const int32_t* __restrict__ start,
-          const int32_t* __restrict__ sidx, const double* __restrict__ sx,
+          const int32_t* __restrict__ sidx, const double* __restrict__ sx, const float4* __restrict__ sxf,
           int32_t* __restrict__ ell_idx, int* __restrict__ err) {
-    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= nrows_total) return;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nrows_total) return;
+    const int q = sidx[t];
+    const int64_t r = node_row[q];
     int grp = group_of_row(gi, r);
     int n = gi.n[grp];
     int K = n - 1;
     int64_t lr = r - gi.row_begin[grp];
-    int q = row_node[r];
     double qx = X[3 * (int64_t)q], qy = X[3 * (int64_t)q + 1], qz = X[3 * (int64_t)q + 2];
+    const float qxf = (float)qx, qyf = (float)qy, qzf = (float)qz;
+    float kth_f = INFINITY;   // float32 bound on the current (n-1)-th key
     int c0[3] = {cell_coord(qx, g.lo[0], g.inv_h, g.G[0]), cell_coord(qy, g.lo[1], g.inv_h, g.G[1]),
                  cell_coord(qz, g.lo[2], g.inv_h, g.G[2])};
     double qc[3] = {qx, qy, qz};
@@ -192,6 +204,14 @@ knn_query(const double* __restrict__ X, const int32_t* __restrict__ row_node, in
                     int c = (cz * g.G[1] + cy) * g.G[0] + cx;
                     int p0 = start[c], p1 = start[c + 1];
                     for (int p = p0; p < p1; ++p) {
+                        // float32 screen.  With every coordinate difference off by
+                        // at most delta in float32, |d2_f32 - d2| <= 2 sqrt(3) delta |d|
+                        // + 3 delta^2 + 2e-7 d2, so a candidate whose float32 d2
+                        // exceeds the bound below cannot enter the exact top list
+                        float4 c = __ldg(sxf + p);
+                        float fx = c.x - qxf, fy = c.y - qyf, fz = c.z - qzf;
+                        float d2f = fx * fx + fy * fy + fz * fz;
+                        if (d2f > kth_f) continue;   // certainly beyond the current list
                         int j = sidx[p];
                         if (j == q) continue;
                         double d2 = sq_dist(qx, qy, qz, sx[3 * (int64_t)p], sx[3 * (int64_t)p + 1],
@@ -205,6 +225,11 @@ knn_query(const double* __restrict__ X, const int32_t* __restrict__ row_node, in
                         }
                         bd[i] = d2;
                         bi[i] = j;
+                        if (cnt == K) {
+                            double kth = bd[K - 1];
+                            kth_f = (float)(kth * (1.0 + 1e-6) + 4.0 * g.delta * sqrt(kth) +
+                                            4.0 * g.delta * g.delta) * (1.0f + 1e-6f);
+                        }
                     }
                 }
             }
@@ -293,9 +318,16 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     for (int a = 0; a < 3; ++a) g.lo[a] = bb[a];
     g.h = h;
     g.inv_h = 1.0 / h;
+    // float32 rounding of two coordinates of magnitude <= M and of their
+    // difference: at most 2^-24 (2 M + |dx|) <= 2^-23 * 1.5 M; doubled margin
+    double M = 0.0;
+    for (int a = 0; a < 6; ++a) M = std::max(M, std::fabs(bb[a]));
+    g.delta = 4.0 * 1.5 * M * std::ldexp(1.0, -24);
 
     int32_t *cell = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *sidx = nullptr;
     double* sx = nullptr;
+    float4* sxf = nullptr;
+    int32_t* node_row = nullptr;
     int* err = nullptr;
     RBFFD_CUDA_TRY(cudaMallocAsync(&cell, N * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMallocAsync(&count, (total + 1) * sizeof(int32_t), st));
@@ -303,6 +335,8 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     RBFFD_CUDA_TRY(cudaMallocAsync(&cursor, total * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMallocAsync(&sidx, N * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMallocAsync(&sx, N * 3 * sizeof(double), st));
+    RBFFD_CUDA_TRY(cudaMallocAsync(&sxf, N * sizeof(float4), st));
+    RBFFD_CUDA_TRY(cudaMallocAsync(&node_row, N * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMallocAsync(&err, sizeof(int), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(count, 0, (total + 1) * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(cursor, 0, total * sizeof(int32_t), st));
@@ -313,11 +347,13 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     RBFFD_CUDA_TRY(cudaGetLastError());
     rbffd_status rs = exclusive_scan(count, start, total + 1, st);
     if (rs != RBFFD_OK) return rs;
-    scatter_nodes<<<nbN, 256, 0, st>>>(nodes, N, cell, start, cursor, sidx, sx);
+    scatter_nodes<<<nbN, 256, 0, st>>>(nodes, N, cell, start, cursor, sidx, sx, sxf);
+    note_launch();
+    invert_rows<<<nbN, 256, 0, st>>>(op->row_node, N, node_row);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
-    knn_query<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(nodes, op->row_node, N, op->gi, g, start,
-                                                            sidx, sx, op->idx, err);
+    knn_query<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(nodes, node_row, N, op->gi, g, start,
+                                                            sidx, sx, sxf, op->idx, err);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     int herr = 0;
@@ -329,6 +365,8 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     cudaFreeAsync(cursor, st);
     cudaFreeAsync(sidx, st);
     cudaFreeAsync(sx, st);
+    cudaFreeAsync(sxf, st);
+    cudaFreeAsync(node_row, st);
     cudaFreeAsync(err, st);
     if (herr) {
         set_error("stencil search found fewer than n-1 neighbours");

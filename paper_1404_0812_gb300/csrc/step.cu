@@ -178,6 +178,16 @@ __device__ __forceinline__ void react(const Args<T>& a, T u, T v, T& f, T& g) {
     }
 }
 
+__device__ __forceinline__ void load4(const float* p, float (&w)[4]) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&w)[4]) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+
 // (L x0)_row and (L x1)_row in one pass over the row (x read L1-bypassing)
 template <typename T>
 __device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, const T* x0, const T* x1, bool two,
@@ -190,11 +200,12 @@ __device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, const T* x0,
         const int64_t e = base + (int64_t)(jb >> 2) * 128;
         int4 iv = __ldg(reinterpret_cast<const int4*>(a.idx + e));
         int ii[4] = {iv.x, iv.y, iv.z, iv.w};
+        T wv[4];
+        load4(a.w + e, wv);   // one (float) or two (double) 16-byte loads
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            T w = __ldg(a.w + e + q);
-            s0 = fma(w, ldcg(x0 + ii[q]), s0);
-            if (two) s1 = fma(w, ldcg(x1 + ii[q]), s1);
+            s0 = fma(wv[q], ldcg(x0 + ii[q]), s0);
+            if (two) s1 = fma(wv[q], ldcg(x1 + ii[q]), s1);
         }
     }
     y0 = s0;

@@ -107,6 +107,14 @@ extern "C" rbffd_status rbffd_autotune_build(const double* nodes, const double* 
         if (best_ms) *best_ms = -1.0;
         return RBFFD_OK;
     }
+    // every candidate must see several stencils per lane, or the timing
+    // measures the tail of the persistent loop instead of its throughput
+    const int cand_t[] = {64, 128, 128, 64};
+    const int cand_b[] = {4, 2, 3, 6};
+    const int ncand = 4;
+    int64_t max_lanes = 0;
+    for (int c = 0; c < ncand; ++c) max_lanes = std::max<int64_t>(max_lanes, (int64_t)cand_t[c] * cand_b[c] * sm_count());
+    sample = std::min<int64_t>(N, std::max<int64_t>(sample, 8 * max_lanes));
     int64_t stride = std::max<int64_t>(1, N / sample);
     int64_t m = (N + stride - 1) / stride;
     double *Xs = nullptr, *Ns = nullptr;
@@ -117,13 +125,12 @@ extern "C" rbffd_status rbffd_autotune_build(const double* nodes, const double* 
     gather_stride<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(nodes, normals, n_per_node, stride, m, Xs, Ns, Ps);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
-    const int cand_t[] = {64, 128};
-    const int cand_b[] = {1, 2, 3, 4, 6};
     double best = 1e300;
     int bt = 128, bb = 2;
     rbffd_status result = RBFFD_OK;
-    for (int t : cand_t) {
-        for (int b : cand_b) {
+    for (int c = 0; c < ncand; ++c) {
+        const int t = cand_t[c], b = cand_b[c];
+        {
             rbffd_build_opts oc = o;
             oc.eps_override = nullptr;
             oc.block_threads = t;

