@@ -776,10 +776,11 @@ __device__ inline void finish(Search& s, double x, double k, int status) {
 //  * learned first guess: accepted when kappa is inside the band;
 //  * Newton step dx = -f/d (slope model if d is unusable), clamped to +-3,
 //    replaced by bisection of the bracket when it would leave it;
-//  * stop when |dx| < xtol/2, when the bracket is narrower than xtol, or
-//    when the steps stop shrinking at the float64 noise floor of kappa
-//    (|dx| < xtol and at least 0.9 of the previous step); every stop returns
-//    the evaluated x, within xtol of the root (the oracle's Brent guarantee).
+//  * stop when the distance to the root is below xtol/2, when the bracket
+//    is narrower than xtol, or when the steps stop shrinking at the float64
+//    noise floor of kappa (distance below xtol, step at least 0.9 of the
+//    previous one); every stop returns the evaluated x, within xtol of the
+//    root (the oracle's Brent guarantee).
 __device__ void search_update(Search& s, double f, double d, double k, double tol_s, int max_evals,
                               double acc_lo, double acc_hi, bool learned, int n) {
     s.evals++;
@@ -798,20 +799,28 @@ __device__ void search_update(Search& s, double f, double d, double k, double to
     // slope model (a Ritz vector from a clustered pair can be poor)
     const double sm = slope_model(n);
     const bool usable = isfinite(d) && isfinite(f) && f != F_FAIL && d <= 0.2 * sm && d >= 5.0 * sm;
-    double dx = clampd(-f / (usable ? d : sm), -3.0, 3.0);
+    const double sl = usable ? d : sm;
+    double dx = clampd(-f / sl, -3.0, 3.0);
     double xn = x + dx;
     const bool bracketed = isfinite(s.lo) && isfinite(s.hi);
     // safeguard: bisect when the Newton point leaves the bracket, or when the
     // last Newton step did not halve |F| (the bracket then still shrinks
     // geometrically, whatever the quality of the slope)
     const bool slow = s.phase == PH_NEWTON && fabs(f) > 0.5 * s.f_prev;
-    if (bracketed && (!(xn > s.lo && xn < s.hi) || slow)) {
+    const bool bisect = bracketed && (!(xn > s.lo && xn < s.hi) || slow);
+    if (bisect) {
         xn = 0.5 * (s.lo + s.hi);
         dx = xn - x;
     }
+    // distance of x from the root: after a bisection x is an end of the
+    // bracket, so at most 2|dx|; after a Newton step |F| over the flatter of
+    // the computed slope and the model (a Ritz vector from a clustered pair
+    // can give a slope several times too steep, and with it a step that
+    // looks converged while x is still far from the root)
+    const double dist = bisect ? fabs(dx) : fabs(f) / fmin(fabs(sl), fabs(sm));
     // every stop returns the evaluated x (its factorisation is still in
-    // scratch for the weights): x is within |dx| (1 + O(dx)) of the root
-    if (usable && fabs(dx) < 0.5 * xtol) {
+    // scratch for the weights)
+    if (usable && dist < 0.5 * xtol) {
         finish(s, x, k, RBFFD_STENCIL_OK);
         return;
     }
@@ -823,7 +832,7 @@ __device__ void search_update(Search& s, double f, double d, double k, double to
     // linearly converging Newton, e.g. with a slope off by 2x, shrinks its
     // steps by a constant factor and does not stop here; when it is slow the
     // halving test above bisects instead)
-    if (s.phase == PH_NEWTON && usable && fabs(dx) < xtol && fabs(dx) >= 0.9 * fabs(s.dx_prev)) {
+    if (s.phase == PH_NEWTON && usable && dist < xtol && fabs(dx) >= 0.9 * fabs(s.dx_prev)) {
         finish(s, x, k, RBFFD_STENCIL_OK);
         return;
     }
