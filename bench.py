@@ -190,6 +190,9 @@ def _file_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
+TRAIN_STATS = {}
+
+
 def train_networks(R, W, T, torch, pairs=200_000):
     """One eps network per stencil size, trained on plain-search eps of
     Fibonacci spheres (100k and 400k nodes) and staggered tori (m = 60 and
@@ -212,9 +215,23 @@ def train_networks(R, W, T, torch, pairs=200_000):
         Y = torch.cat(Y)
         sel = torch.randperm(F.shape[0], generator=gen, device="cuda")[:pairs]
         net = R.EpsNet(n, W.mlp_pack(W.mlp_init(3 * n, seed=n)).astype(np.float32))
-        net.train(F[sel].contiguous(), Y[sel].contiguous(), epochs=30, batch=1024, lr=1e-3, seed=0)
+        Fs, Ys = F[sel].contiguous(), Y[sel].contiguous()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        losses = net.train(Fs, Ys, epochs=30, batch=1024, lr=1e-3, seed=0)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        # forward + backward of 3n -> 64 -> 64 -> 1 per sample: 3 x 2 x weights
+        flops = 30 * Fs.shape[0] * 3 * 2 * (3 * n * 64 + 64 * 64 + 64)
+        TRAIN_STATS[int(n)] = {"pairs": int(Fs.shape[0]), "epochs": 30, "ms": round(ms, 1),
+                               "samples_per_s": round(30 * Fs.shape[0] / (ms * 1e-3), 1),
+                               "tflops": round(flops / (ms * 1e-3) / 1e12, 3),
+                               "loss_first_last": [round(losses[0], 5), round(losses[-1], 5)]}
         nets.append(net)
-        del F, Y
+        del F, Y, Fs, Ys
     return nets
 
 
@@ -580,6 +597,7 @@ def run_ours(args):
                             "accepted_fraction": round(float((info["status"] == 4).mean()), 4)},
         "apply": apply,
         "imex_step": step_info,
+        "mlp_train": TRAIN_STATS or None,
         "all_stencils_ok": ok,
         "other_configs": configs,
         "e2e": {"value": round(N_NODES / statistics.mean(e2e_times), 1), "unit": UNIT,

@@ -72,10 +72,14 @@ typedef struct {
     const rbffd_mlp* mlp[RBFFD_MAX_GROUPS]; /* learned networks (may be NULL) */
     int block_threads;        /* 0 = autotuned / default launch shape */
     int blocks_per_sm;        /* 0 = autotuned / default launch shape */
+    double eps_lo;            /* search range of the dimensionless eps * r_s */
+    double eps_hi;            /*   (r_s = the stencil's largest centre distance);
+                                 0 = unbounded on that side.  A stencil whose
+                                 root lies outside gets RBFFD_STENCIL_NO_BRACKET */
 } rbffd_build_opts;
 
 /* Fill opts with defaults: IMQ, kappa_T 1e12, eps_tol 1e-4, max_evals 64,
- * no learned start, band [0.5, 2]. */
+ * no learned start, band [0.5, 2], unbounded eps range. */
 void rbffd_build_opts_default(rbffd_build_opts* opts);
 
 /*
@@ -151,21 +155,29 @@ typedef struct {
     double tol;         /* BiCGSTAB relative residual tolerance */
     int maxit;          /* BiCGSTAB iteration cap per solve */
     int use_graph;      /* 1: replay each step from a captured CUDA graph */
+    int order;          /* SBDF order 1..4 (0 = 2, the SBDF2 of Section 7;
+                           4 = the BDF4 of Section 6 with explicit kinetics) */
 } rbffd_step_params;
 
 /*
  * State of an IMEX run.  All vectors are caller-owned device arrays of N
  * values of params.dtype.  u, v: current solution (updated in place);
- * u_prev, v_prev, f_prev, g_prev: SBDF2 history (u^{n-1}, v^{n-1},
- * f(u^{n-1}, v^{n-1}), g(...)); has_history = 0 makes the next step IMEX
- * Euler, after which the call sets it to 1.  v, v_prev, g_prev may be NULL
- * when nspecies = 1.
+ * u_prev, v_prev, f_prev, g_prev: the past level n-1 (u^{n-1}, v^{n-1},
+ * f(u^{n-1}, v^{n-1}), g(...)); *_prev2 and *_prev3 the levels n-2 and n-3
+ * (needed for order 3 / 4 only, else may be NULL).  has_history = the number
+ * of valid past levels: a step of order k uses min(k, has_history + 1)
+ * (0 makes it IMEX Euler; a run without history climbs one order per step,
+ * or the caller fills the past levels, e.g. from an exact solution, and sets
+ * has_history = k - 1); the call updates it.  v and the v_ / g_ levels may
+ * be NULL when nspecies = 1.
  */
 typedef struct {
     void* u; void* v;
     void* u_prev; void* v_prev; void* f_prev; void* g_prev;
     int has_history;
     int64_t step;       /* steps taken so far (updated) */
+    void* u_prev2; void* v_prev2; void* f_prev2; void* g_prev2;
+    void* u_prev3; void* v_prev3; void* f_prev3; void* g_prev3;
 } rbffd_state;
 
 typedef struct {
@@ -180,8 +192,12 @@ typedef struct {
  * rbffd_step_imex - advance the semi-discrete reaction-diffusion system
  * d/dt u = delta_u L_X u + f(u,v), d/dt v = delta_v L_X v + g(u,v)
  * (Eq. kernel_mol; Eqs. turing1/turing2 for the paper's kinetics) by nsteps
- * steps of SBDF2 (first step IMEX Euler without history):
+ * steps of the semi-implicit BDF of params->order (SBDFk, Ascher-Ruuth-Wetton:
+ * diffusion implicit, kinetics extrapolated), e.g. for k = 2
  *   (3 I - 2 dt delta L) u^{n+1} = 4 u^n - u^{n-1} + 2 dt (2 f^n - f^{n-1}),
+ * and for k = 4
+ *   (25 I - 12 dt delta L) u^{n+1} = 48 u^n - 36 u^{n-1} + 16 u^{n-2} - 3 u^{n-3}
+ *                                    + 12 dt (4 f^n - 6 f^{n-1} + 4 f^{n-2} - f^{n-3}),
  * each implicit system solved by BiCGSTAB from x0 = u^n (Section 4.2).
  * One cooperative persistent launch per step (optionally replayed from a
  * CUDA graph).  Synchronises the stream at the end and fills report (may be
@@ -200,6 +216,38 @@ rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* state, const rbffd_step_
  */
 rbffd_status rbffd_get_stencil_info(const rbffd_op* op, double* eps, double* kappa,
                                     int32_t* evals, int32_t* status, void* stream);
+
+/* eps, kappa and evals of rbffd_get_stencil_info (Section 5), without the
+ * status array. */
+rbffd_status rbffd_get_eps(const rbffd_op* op, double* eps, double* kappa, int32_t* evals,
+                           void* stream);
+
+/*
+ * Borrowed views of the operator's storage (Section 4.1's N x n weight
+ * matrix, stored as sliced ELL), valid until rbffd_destroy(op).  Rows are
+ * grouped by stencil size (groups by descending n); operator row r of group
+ * g (row_begin[g] <= r < row_begin[g+1]) is row row_node[r] of L_X.  Entry j
+ * (0 <= j < npad[g]) of the group's local row q = r - row_begin[g] is element
+ *   elem_begin[g] + (q / 32) * 32 * npad[g] + (j / 4) * 128 + (q % 32) * 4 + j % 4
+ * of idx (int32 column = node index), w64 (float64 weight) and w32 (its
+ * float32 copy); entries j >= n[g] hold the row's own node and weight 0,
+ * and the rows that pad a group's last slice of 32 hold index 0 and weight
+ * 0 (every index is a valid node).  All pointers are device memory
+ * owned by op; the call itself touches no device memory.
+ */
+typedef struct {
+    int ngroups;
+    int n[RBFFD_MAX_GROUPS];
+    int npad[RBFFD_MAX_GROUPS];                /* n rounded up to a multiple of 4 */
+    int64_t row_begin[RBFFD_MAX_GROUPS + 1];
+    int64_t elem_begin[RBFFD_MAX_GROUPS + 1];
+    int64_t elems;                             /* total elements, padding included */
+    const int32_t* row_node;                   /* N */
+    const int32_t* idx;
+    const double* w64;
+    const float* w32;
+} rbffd_ell_view;
+rbffd_status rbffd_get_ell(const rbffd_op* op, rbffd_ell_view* view);
 
 /*
  * Operator rows in node order as dense padded arrays (device outputs):
@@ -288,6 +336,9 @@ int64_t rbffd_mlp_param_count(int n);
  * above; NULL = zeros). */
 rbffd_status rbffd_mlp_create(int n, const float* params_host, rbffd_mlp** out);
 rbffd_status rbffd_mlp_get_params(const rbffd_mlp* mlp, float* params_host);
+/* Replace a network's parameters with host float32 params (layout above;
+ * param_count floats) and reset its Adam state.  Synchronous. */
+rbffd_status rbffd_mlp_load(rbffd_mlp* mlp, const float* params_host);
 void rbffd_mlp_destroy(rbffd_mlp* mlp);
 
 /*

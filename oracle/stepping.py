@@ -4,10 +4,17 @@ Semi-discrete system (Eq. kernel_mol; Eq. diffusion_scalar writes the
 coefficient as nu, the text as delta: the same quantity):
     d/dt u = delta_u L_X u + f(u, v),   d/dt v = delta_v L_X v + g(u, v).
 
-Time stepping (Section 7 names SBDF2 with the diffusion implicit; the formula
-is not printed, so the standard second-order semi-implicit BDF is used):
-    (3 I - 2 dt delta L) u^{n+1} = 4 u^n - u^{n-1} + 2 dt (2 f^n - f^{n-1}),
-with a first step of IMEX Euler, (I - dt delta L) u^1 = u^0 + dt f^0.
+Time stepping (Section 7 names SBDF2 with the diffusion implicit; Section 6
+steps the diffusion equations with BDF4; neither formula is printed, so the
+standard semi-implicit BDF family SBDFk of Ascher, Ruuth and Wetton (SIAM J.
+Numer. Anal. 32, 1995) is used):
+    alpha_k u^{n+1} - dt delta L u^{n+1} = sum_j a_kj u^{n-j} + dt sum_j b_kj f^{n-j},
+j = 0 .. k-1, with the coefficients in SBDF below; for k = 2 this is
+    (3 I - 2 dt delta L) u^{n+1} = 4 u^n - u^{n-1} + 2 dt (2 f^n - f^{n-1})
+(up to the factor 2).  A run of order k whose history holds fewer than k - 1
+past levels takes its first steps at orders 1, 2, ... (IMEX Euler first), or
+starts from caller-given past levels (Section 6 bootstraps BDF4 from the exact
+solution).
 Each implicit system is solved by BiCGSTAB (Section 4.2, Section 6), in the
 textbook form of van der Vorst (1992) as laid out in the Barrett et al.
 "Templates" book, with x0 = u^n and the relative residual ||b - A x||_2 /
@@ -90,31 +97,50 @@ def bicgstab(matvec, b: np.ndarray, x0: np.ndarray, tol: float, maxit: int):
     return x, maxit, np.linalg.norm(r) / bnorm, False
 
 
+# SBDFk: k -> (alpha_k, a_k0 .. a_k,k-1 (on u^{n-j}), b_k0 .. b_k,k-1 (on f^{n-j}))
+SBDF = {
+    1: (1.0, (1.0,), (1.0,)),
+    2: (3.0 / 2.0, (2.0, -1.0 / 2.0), (2.0, -1.0)),
+    3: (11.0 / 6.0, (3.0, -3.0 / 2.0, 1.0 / 3.0), (3.0, -3.0, 1.0)),
+    4: (25.0 / 12.0, (4.0, -3.0, 4.0 / 3.0, -1.0 / 4.0), (4.0, -6.0, 4.0, -1.0)),
+}
+
+
 def imex_run(L_apply, u0, v0, p: dict, nsteps: int, tol: float = 1e-12,
-             maxit: int = 200, history=None):
-    """Advance (u, v) by ``nsteps`` IMEX steps (Euler first, then SBDF2).
+             maxit: int = 200, history=None, order: int = 2):
+    """Advance (u, v) by ``nsteps`` SBDF steps of the given order (1..4).
 
     ``L_apply(x)`` returns L_X x.  ``v0`` may be None for one species.
-    ``history`` = (u_prev, v_prev, f_prev, g_prev) continues an SBDF2 run.
-    Returns dict(u, v, history, iters=list of (iters_u, iters_v)).
+    ``history``: None, one past level (u_prev, v_prev, f_prev, g_prev), or a
+    list of past levels, most recent first (f, g the kinetics at that level;
+    None entries for a missing second species).  Returns dict(u, v,
+    history = the most recent past level, levels = all kept past levels,
+    iters = list of (iters_u, iters_v)).
     """
+    if order not in SBDF:
+        raise ValueError("order must be 1, 2, 3 or 4")
     dt, du = p["dt"], p["delta_u"]
     dv = p.get("delta_v", 0.0)
     two = v0 is not None
     u = np.asarray(u0, dtype=np.float64).copy()
     v = np.asarray(v0, dtype=np.float64).copy() if two else np.zeros_like(u)
-    hist = history
+    if history is None:
+        levels = []
+    elif isinstance(history, tuple):
+        levels = [history]
+    else:
+        levels = list(history)
+    levels = [tuple(np.zeros_like(u) if x is None else np.asarray(x, dtype=np.float64) for x in lv)
+              for lv in levels]
     iters = []
     for _ in range(nsteps):
         f, g = reaction(p, u, v)
-        if hist is None:     # IMEX Euler
-            c0, cl = 1.0, dt
-            bu, bv = u + dt * f, v + dt * g
-        else:                # SBDF2
-            up, vp, fp, gp = hist
-            c0, cl = 3.0, 2.0 * dt
-            bu = 4.0 * u - up + 2.0 * dt * (2.0 * f - fp)
-            bv = 4.0 * v - vp + 2.0 * dt * (2.0 * g - gp)
+        k = min(order, len(levels) + 1)
+        alpha, a, b = SBDF[k]
+        past = [(u, v, f, g)] + levels[:k - 1]
+        bu = sum(a[j] * past[j][0] for j in range(k)) + dt * sum(b[j] * past[j][2] for j in range(k))
+        bv = sum(a[j] * past[j][1] for j in range(k)) + dt * sum(b[j] * past[j][3] for j in range(k))
+        c0, cl = alpha, dt
         Au = lambda x: c0 * x - (cl * du) * L_apply(x)
         un, iu, ru, oku = bicgstab(Au, bu, u, tol, maxit)
         if not oku:
@@ -126,7 +152,8 @@ def imex_run(L_apply, u0, v0, p: dict, nsteps: int, tol: float = 1e-12,
                 raise RuntimeError(f"BiCGSTAB (v) failed: relres {rv}")
         else:
             vn, iv = v, 0
-        hist = (u, v, f, g)
+        levels = ([(u, v, f, g)] + levels)[:order - 1]
         u, v = un, vn
         iters.append((iu, iv))
-    return dict(u=u, v=v if two else None, history=hist, iters=iters)
+    return dict(u=u, v=v if two else None, history=levels[0] if levels else None, levels=levels,
+                iters=iters)

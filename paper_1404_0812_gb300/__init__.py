@@ -2,7 +2,7 @@
 
 Python binding of the C ABI in ``include/rbffd.h``, with the same names:
 ``build_operator``, ``apply``, ``step_imex``, ``get_stencil_info``,
-``get_rows``, ``destroy`` and the learned-eps calls.  The functions only
+``get_eps``, ``get_ell``, ``get_rows``, ``destroy`` and the learned-eps calls.  The functions only
 marshal arguments (torch tensors provide device memory and streams); all
 arithmetic runs in the CUDA library, and a missing library is an error.
 """
@@ -65,9 +65,11 @@ class Operator:
 
 def build_operator(nodes, normals, n=31, kernel="imq", kappa_target=1e12, eps_tol=1e-4,
                    max_evals=64, eps_override=None, mlps=None, accept=(0.5, 2.0),
-                   block_threads=0, blocks_per_sm=0, stream=None, allow_failures=False):
+                   block_threads=0, blocks_per_sm=0, stream=None, allow_failures=False,
+                   eps_range=(0.0, 0.0)):
     """rbffd_build_operator.  ``n`` is an int or a CUDA int32 tensor (N,);
-    ``mlps`` a list of EpsNet to warm-start the search."""
+    ``mlps`` a list of EpsNet to warm-start the search; ``eps_range`` the
+    search range of eps * r_s (0 = unbounded on that side)."""
     lib = _lib.load()
     nodes = _dev(nodes, torch.float64)
     normals = _dev(normals, torch.float64)
@@ -87,6 +89,7 @@ def build_operator(nodes, normals, n=31, kernel="imq", kappa_target=1e12, eps_to
         for i, m in enumerate(mlps):
             o.mlp[i] = m.handle
     o.block_threads, o.blocks_per_sm = int(block_threads), int(blocks_per_sm)
+    o.eps_lo, o.eps_hi = float(eps_range[0]), float(eps_range[1])
     if isinstance(n, torch.Tensor):
         npn = _dev(n, torch.int32)
         nptr, nu = C.c_void_p(npn.data_ptr()), 0
@@ -171,6 +174,43 @@ def get_stencil_info(op: Operator, stream=None):
     return out
 
 
+def get_eps(op: Operator, stream=None):
+    """rbffd_get_eps -> (eps float64, kappa float64, evals int32) CUDA tensors."""
+    lib = _lib.load()
+    eps = torch.empty(op.N, dtype=torch.float64, device="cuda")
+    kappa = torch.empty(op.N, dtype=torch.float64, device="cuda")
+    evals = torch.empty(op.N, dtype=torch.int32, device="cuda")
+    _lib.check(lib.rbffd_get_eps(op.handle, _ptr(eps), _ptr(kappa), _ptr(evals), _stream(stream)),
+               "rbffd_get_eps")
+    return eps, kappa, evals
+
+
+class _DeviceView:
+    """Zero-copy wrapper of a library-owned device array (borrowed; valid
+    while its operator lives)."""
+
+    def __init__(self, ptr, count, typestr, owner):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 2}
+        self._owner = owner
+
+
+def get_ell(op: Operator):
+    """rbffd_get_ell -> dict with the sliced-ELL layout (ngroups, n, npad,
+    row_begin, elem_begin, elems) and borrowed CUDA tensors row_node, idx,
+    w64, w32 that alias the operator's storage (keep ``op`` alive)."""
+    lib = _lib.load()
+    v = _lib.EllView()
+    _lib.check(lib.rbffd_get_ell(op.handle, C.byref(v)), "rbffd_get_ell")
+    G = v.ngroups
+    out = dict(ngroups=G, n=list(v.n[:G]), npad=list(v.npad[:G]), row_begin=list(v.row_begin[:G + 1]),
+               elem_begin=list(v.elem_begin[:G + 1]), elems=int(v.elems))
+    for name, count, ts in (("row_node", op.N, "<i4"), ("idx", v.elems, "<i4"),
+                            ("w64", v.elems, "<f8"), ("w32", v.elems, "<f4")):
+        out[name] = torch.as_tensor(_DeviceView(getattr(v, name), count, ts, op), device="cuda")
+    return out
+
+
 def get_rows(op: Operator, stream=None):
     """rbffd_get_rows -> (idx int32 N x n_max, w float64 N x n_max)."""
     lib = _lib.load()
@@ -211,6 +251,7 @@ class StepParams:
     tol: float = 1e-12
     maxit: int = 200
     use_graph: bool = False
+    order: int = 2          # SBDF order 1..4
 
 
 @dataclass
@@ -224,11 +265,24 @@ class StepState:
     g_prev: torch.Tensor | None = None
     has_history: int = 0
     step: int = 0
+    u_prev2: torch.Tensor | None = None
+    v_prev2: torch.Tensor | None = None
+    f_prev2: torch.Tensor | None = None
+    g_prev2: torch.Tensor | None = None
+    u_prev3: torch.Tensor | None = None
+    v_prev3: torch.Tensor | None = None
+    f_prev3: torch.Tensor | None = None
+    g_prev3: torch.Tensor | None = None
 
     @staticmethod
-    def create(u, v=None):
+    def create(u, v=None, order=2):
         z = lambda t: None if t is None else torch.zeros_like(t)
-        return StepState(u=u, v=v, u_prev=z(u), v_prev=z(v), f_prev=z(u), g_prev=z(v))
+        s = StepState(u=u, v=v, u_prev=z(u), v_prev=z(v), f_prev=z(u), g_prev=z(v))
+        if order >= 3:
+            s.u_prev2, s.v_prev2, s.f_prev2, s.g_prev2 = z(u), z(v), z(u), z(v)
+        if order >= 4:
+            s.u_prev3, s.v_prev3, s.f_prev3, s.g_prev3 = z(u), z(v), z(u), z(v)
+        return s
 
 
 def model_coefs(p: dict):
@@ -257,8 +311,11 @@ def step_imex(op: Operator, state: StepState, params: StepParams, nsteps: int, s
     for i, c in enumerate(params.coef):
         sp.coef[i] = c
     sp.tol, sp.maxit, sp.use_graph = params.tol, params.maxit, int(params.use_graph)
+    sp.order = int(params.order)
     cs = _lib.State(_ptr(state.u), _ptr(state.v), _ptr(state.u_prev), _ptr(state.v_prev),
-                    _ptr(state.f_prev), _ptr(state.g_prev), state.has_history, state.step)
+                    _ptr(state.f_prev), _ptr(state.g_prev), state.has_history, state.step,
+                    _ptr(state.u_prev2), _ptr(state.v_prev2), _ptr(state.f_prev2), _ptr(state.g_prev2),
+                    _ptr(state.u_prev3), _ptr(state.v_prev3), _ptr(state.f_prev3), _ptr(state.g_prev3))
     rep = _lib.StepReport()
     st = lib.rbffd_step_imex(op.handle, C.byref(cs), C.byref(sp), int(nsteps), _stream(stream),
                              C.byref(rep))
@@ -311,6 +368,16 @@ class EpsNet:
         _lib.check(_lib.load().rbffd_mlp_get_params(self.handle, out.ctypes.data_as(C.c_void_p)),
                    "rbffd_mlp_get_params")
         return out
+
+    def load(self, params):
+        """rbffd_mlp_load: replace the parameters (host float32, param_count
+        values) and reset the Adam state."""
+        import numpy as np
+        buf = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if buf.size != self.P:
+            raise ValueError(f"expected {self.P} parameters, got {buf.size}")
+        _lib.check(_lib.load().rbffd_mlp_load(self.handle, buf.ctypes.data_as(C.c_void_p)),
+                   "rbffd_mlp_load")
 
     def loss_grad(self, feats, target, stream=None):
         """rbffd_mlp_loss_grad -> (grad CUDA float32 tensor, loss float)."""

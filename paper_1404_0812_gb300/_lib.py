@@ -27,18 +27,28 @@ class BuildOpts(C.Structure):
                 ("max_evals", C.c_int), ("use_learned", C.c_int), ("accept_lo", C.c_double),
                 ("accept_hi", C.c_double), ("eps_override", vp),
                 ("mlp", vp * RBFFD_MAX_GROUPS), ("block_threads", C.c_int),
-                ("blocks_per_sm", C.c_int)]
+                ("blocks_per_sm", C.c_int), ("eps_lo", C.c_double), ("eps_hi", C.c_double)]
+
+
+class EllView(C.Structure):
+    _fields_ = [("ngroups", C.c_int), ("n", C.c_int * RBFFD_MAX_GROUPS),
+                ("npad", C.c_int * RBFFD_MAX_GROUPS),
+                ("row_begin", C.c_int64 * (RBFFD_MAX_GROUPS + 1)),
+                ("elem_begin", C.c_int64 * (RBFFD_MAX_GROUPS + 1)), ("elems", C.c_int64),
+                ("row_node", vp), ("idx", vp), ("w64", vp), ("w32", vp)]
 
 
 class StepParams(C.Structure):
     _fields_ = [("model", C.c_int), ("nspecies", C.c_int), ("dtype", C.c_int), ("dt", C.c_double),
                 ("delta_u", C.c_double), ("delta_v", C.c_double), ("coef", C.c_double * 8),
-                ("tol", C.c_double), ("maxit", C.c_int), ("use_graph", C.c_int)]
+                ("tol", C.c_double), ("maxit", C.c_int), ("use_graph", C.c_int), ("order", C.c_int)]
 
 
 class State(C.Structure):
     _fields_ = [("u", vp), ("v", vp), ("u_prev", vp), ("v_prev", vp), ("f_prev", vp),
-                ("g_prev", vp), ("has_history", C.c_int), ("step", C.c_int64)]
+                ("g_prev", vp), ("has_history", C.c_int), ("step", C.c_int64),
+                ("u_prev2", vp), ("v_prev2", vp), ("f_prev2", vp), ("g_prev2", vp),
+                ("u_prev3", vp), ("v_prev3", vp), ("f_prev3", vp), ("g_prev3", vp)]
 
 
 class StepReport(C.Structure):
@@ -60,6 +70,8 @@ SIGNATURES = {
                                   C.POINTER(StepReport)]),
     "rbffd_get_stencil_info": (C.c_int, [vp, vp, vp, vp, vp, vp]),
     "rbffd_get_rows": (C.c_int, [vp, vp, vp, vp]),
+    "rbffd_get_eps": (C.c_int, [vp, vp, vp, vp, vp]),
+    "rbffd_get_ell": (C.c_int, [vp, C.POINTER(EllView)]),
     "rbffd_get_build_timings": (C.c_int, [vp, C.POINTER(C.c_double)]),
     "rbffd_launch_count": (C.c_int64, []),
     "rbffd_op_nodes": (C.c_int64, [vp]),
@@ -70,6 +82,7 @@ SIGNATURES = {
     "rbffd_mlp_param_count": (C.c_int64, [C.c_int]),
     "rbffd_mlp_create": (C.c_int, [C.c_int, vp, C.POINTER(vp)]),
     "rbffd_mlp_get_params": (C.c_int, [vp, vp]),
+    "rbffd_mlp_load": (C.c_int, [vp, vp]),
     "rbffd_mlp_destroy": (None, [vp]),
     "rbffd_features": (C.c_int, [vp, vp, vp, C.c_int, vp, vp, C.POINTER(C.c_int64), vp]),
     "rbffd_mlp_loss_grad": (C.c_int, [vp, vp, vp, C.c_int64, vp, vp, vp]),

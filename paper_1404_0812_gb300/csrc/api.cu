@@ -145,6 +145,9 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     RBFFD_CHECK_ARG(o.eps_override || o.eps_tol > 0.0, "eps_tol must be > 0");
     RBFFD_CHECK_ARG(o.eps_override || o.max_evals >= 2, "max_evals must be >= 2");
     RBFFD_CHECK_ARG(!o.use_learned || (o.accept_lo > 0 && o.accept_hi >= o.accept_lo), "accept band");
+    RBFFD_CHECK_ARG(o.eps_lo >= 0.0 && o.eps_hi >= 0.0 && std::isfinite(o.eps_lo) && std::isfinite(o.eps_hi),
+                    "eps_lo / eps_hi must be finite and >= 0");
+    RBFFD_CHECK_ARG(o.eps_lo == 0.0 || o.eps_hi == 0.0 || o.eps_lo < o.eps_hi, "eps_lo must be < eps_hi");
     cudaStream_t st = as_stream(stream);
 
     // ---- stencil-size groups (sorted by descending n; stable node order)
@@ -261,6 +264,7 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
         TRY_OP(cudaEventRecord(ev[2], st));
         s = build_search(op, nodes, normals, o, guess, st);
         TRY_OP(cudaEventRecord(ev[3], st));
+        TRY_OP(cudaEventRecord(ev[4], st));   // no separate weights phase
         if (guess) cudaFreeAsync(guess, st);
         if (s != RBFFD_OK) return fail(s);
         int* bad = nullptr;
@@ -285,10 +289,10 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     if (o.eps_override) {
         s = build_weights(op, nodes, normals, o, op->eps, st);
         if (s != RBFFD_OK && s != RBFFD_ESINGULAR) return fail(s);
+        TRY_OP(cudaEventRecord(ev[4], st));
     } else {
         s = RBFFD_OK;
     }
-    TRY_OP(cudaEventRecord(ev[4], st));
     TRY_OP(cudaStreamSynchronize(st));
     for (int i = 0; i < 4; ++i) {
         float ms = 0.f;
@@ -316,6 +320,30 @@ rbffd_status rbffd_get_stencil_info(const rbffd_op* op, double* eps, double* kap
     if (kappa) RBFFD_CUDA_TRY(cudaMemcpyAsync(kappa, op->kappa, op->N * 8, cudaMemcpyDeviceToDevice, st));
     if (evals) RBFFD_CUDA_TRY(cudaMemcpyAsync(evals, op->evals, op->N * 4, cudaMemcpyDeviceToDevice, st));
     if (status) RBFFD_CUDA_TRY(cudaMemcpyAsync(status, op->status, op->N * 4, cudaMemcpyDeviceToDevice, st));
+    return RBFFD_OK;
+}
+
+rbffd_status rbffd_get_eps(const rbffd_op* op, double* eps, double* kappa, int32_t* evals, void* stream) {
+    return rbffd_get_stencil_info(op, eps, kappa, evals, nullptr, stream);
+}
+
+rbffd_status rbffd_get_ell(const rbffd_op* op, rbffd_ell_view* v) {
+    RBFFD_CHECK_ARG(op && v, "NULL argument");
+    memset(v, 0, sizeof(*v));
+    v->ngroups = op->gi.ngroups;
+    for (int g = 0; g < op->gi.ngroups; ++g) {
+        v->n[g] = op->gi.n[g];
+        v->npad[g] = op->gi.npad[g];
+    }
+    for (int g = 0; g <= op->gi.ngroups; ++g) {
+        v->row_begin[g] = op->gi.row_begin[g];
+        v->elem_begin[g] = op->gi.ell_off[g];
+    }
+    v->elems = op->ell_elems;
+    v->row_node = op->row_node;
+    v->idx = op->idx;
+    v->w64 = op->w64;
+    v->w32 = op->w32;
     return RBFFD_OK;
 }
 

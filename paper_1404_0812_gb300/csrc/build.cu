@@ -755,6 +755,7 @@ struct Search {
     double x_ret, k_ret;  // result (eps_s = exp(x_ret)) and kappa reported for it
     double dx_prev;
     double f_prev;        // |F| at the previous iterate
+    double ulo, uhi;      // caller's search range of x (+-inf when none)
     int phase, evals;
     int status;
 };
@@ -794,6 +795,12 @@ __device__ void search_update(Search& s, double f, double d, double k, double to
         return;
     }
     if (f > 0.0) s.lo = fmax(s.lo, x); else s.hi = fmin(s.hi, x);
+    // the root lies outside the caller's range: kappa is still above kappa_T
+    // at its largest eps, or already below it at its smallest
+    if ((f > 0.0 && x >= s.uhi) || (f < 0.0 && x <= s.ulo)) {
+        finish(s, x, k, RBFFD_STENCIL_NO_BRACKET);
+        return;
+    }
     const double xtol = tol_s / exp(x);
     // the Hellmann-Feynman slope is trusted only within a factor 5 of the
     // slope model (a Ritz vector from a clustered pair can be poor)
@@ -808,10 +815,9 @@ __device__ void search_update(Search& s, double f, double d, double k, double to
     // geometrically, whatever the quality of the slope)
     const bool slow = s.phase == PH_NEWTON && fabs(f) > 0.5 * s.f_prev;
     const bool bisect = bracketed && (!(xn > s.lo && xn < s.hi) || slow);
-    if (bisect) {
-        xn = 0.5 * (s.lo + s.hi);
-        dx = xn - x;
-    }
+    if (bisect) xn = 0.5 * (s.lo + s.hi);
+    xn = clampd(xn, s.ulo, s.uhi);
+    dx = xn - x;
     // distance of x from the root: after a bisection x is an end of the
     // bracket, so at most 2|dx|; after a Newton step |F| over the flatter of
     // the computed slope and the model (a Ritz vector from a clustered pair
@@ -967,6 +973,7 @@ struct SearchArgs {
     int lane_size;
     int kernel;
     double kT, tol, acc_lo, acc_hi;
+    double xlo, xhi;             // search range of ln(eps * r_s) (+-inf when none)
     int max_evals;
     const float* guess_rows;     // ln(eps_s) per internal row, or NULL
     unsigned long long* counters;  // per group
@@ -976,7 +983,7 @@ struct SearchArgs {
     int32_t* status;
 };
 
-__global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
+__global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs A) {
     const int lane_id = threadIdx.x & 31;
     const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     Lane S{A.scratch + warp_global * 32 * (int64_t)A.lane_size + lane_id};
@@ -1008,9 +1015,11 @@ __global__ void __launch_bounds__(128) search_kernel(SearchArgs A) {
                 st.hi = INFINITY;
                 st.dx_prev = INFINITY;
                 st.f_prev = INFINITY;
+                st.ulo = A.xlo;
+                st.uhi = A.xhi;
                 float gs = A.guess_rows ? A.guess_rows[r] : NAN;
                 learned = isfinite(gs);
-                st.x_next = learned ? (double)gs : log(1.0 / geo.mean_d);
+                st.x_next = clampd(learned ? (double)gs : log(1.0 / geo.mean_d), A.xlo, A.xhi);
             }
         }
         if (__ballot_sync(0xffffffffu, have) == 0) {
@@ -1077,7 +1086,7 @@ struct WeightArgs {
     int* nfail;
 };
 
-__global__ void __launch_bounds__(128) weights_kernel(WeightArgs A) {
+__global__ void __launch_bounds__(128, 4) weights_kernel(WeightArgs A) {
     const int lane_id = threadIdx.x & 31;
     const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     Lane S{A.scratch + warp_global * 32 * (int64_t)A.lane_size + lane_id};
@@ -1127,7 +1136,10 @@ struct LaunchShape {
 LaunchShape launch_shape(const rbffd_build_opts& o, int64_t rows) {
     LaunchShape ls;
     ls.threads = o.block_threads > 0 ? o.block_threads : 128;
-    int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 2;
+    // 4 x 128 threads: 16 resident warps per SM, which the kernels' launch
+    // bounds (<= 128 registers per thread) allow; more warps in flight hide
+    // more of the latency of the lanes' scratch loads
+    int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 4;
     int64_t want = (int64_t)sm_count() * bps;
     int64_t need = (rows + ls.threads - 1) / ls.threads;
     ls.blocks = (int)std::max<int64_t>(1, std::min(want, need));
@@ -1163,6 +1175,8 @@ rbffd_status build_search(rbffd_op* op, const double* nodes, const double* norma
     A.kernel = o.kernel;
     A.kT = o.kappa_target;
     A.tol = o.eps_tol;
+    A.xlo = o.eps_lo > 0.0 ? log(o.eps_lo) : -INFINITY;
+    A.xhi = o.eps_hi > 0.0 ? log(o.eps_hi) : INFINITY;
     A.acc_lo = o.accept_lo;
     A.acc_hi = o.accept_hi;
     A.max_evals = o.max_evals;

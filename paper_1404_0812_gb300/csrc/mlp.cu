@@ -422,6 +422,16 @@ rbffd_status rbffd_mlp_get_params(const rbffd_mlp* m, float* params_host) {
     return RBFFD_OK;
 }
 
+rbffd_status rbffd_mlp_load(rbffd_mlp* m, const float* params_host) {
+    RBFFD_CHECK_ARG(m && params_host, "NULL argument");
+    RBFFD_CUDA_TRY(cudaMemcpy(m->params, params_host, m->P * sizeof(float), cudaMemcpyHostToDevice));
+    // new parameters start a new optimisation: Adam's moments and step count reset
+    if (m->adam_m) RBFFD_CUDA_TRY(cudaMemset(m->adam_m, 0, m->P * sizeof(float)));
+    if (m->adam_v) RBFFD_CUDA_TRY(cudaMemset(m->adam_v, 0, m->P * sizeof(float)));
+    m->adam_t = 0;
+    return RBFFD_OK;
+}
+
 void rbffd_mlp_destroy(rbffd_mlp* m) {
     if (!m) return;
     cudaFree(m->params);

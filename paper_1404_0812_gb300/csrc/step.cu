@@ -39,7 +39,7 @@ struct rbffd_step_ws {
     int blocks, threads;
     cudaGraphExec_t graph;            // captured step (memset + launch)
     cudaStream_t cap;                 // library-owned stream used only for capture
-    unsigned char graph_args[512];    // kernel arguments the graph holds
+    unsigned char graph_args[1024];   // kernel arguments the graph holds
     size_t graph_args_size;
 };
 
@@ -72,6 +72,9 @@ struct Args {
     GroupInfo gi;
     int64_t N;
     T *u, *v, *up, *vp, *fp, *gp;
+    T *up2, *vp2, *fp2, *gp2;   // levels n-2 and n-3 (SBDF3 / SBDF4 only)
+    T *up3, *vp3, *fp3, *gp3;
+    int order;         // SBDF order 1..4
     T* vec;            // 2 x 7 x N
     int ns;
     int model;
@@ -217,11 +220,17 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool two = a.ns == 2;
-    const bool hist = *((volatile int*)(a.flags + 2)) != 0;
+    // past levels available -> the order of this step (SBDF1 .. SBDF4, the
+    // first steps of a run without history climb one order per step)
+    const int nhist = *((volatile int*)(a.flags + 2));
+    const int ord = min(a.order, nhist + 1);
     const int slot = *((volatile int*)(a.flags + 3));
     unsigned long long target = 0;
-    const T c0 = hist ? T(3) : T(1);
-    const T cl = hist ? T(2) * a.dt : a.dt;
+    // the SBDFk system scaled to integer coefficients:
+    //   c0 u^{n+1} - cl delta L u^{n+1} = sum_j A_j u^{n-j} + cl sum_j B_j f^{n-j}
+    // k = 1: c0 1, cl dt;  k = 2: 3, 2 dt;  k = 3: 11, 6 dt;  k = 4: 25, 12 dt
+    const T c0 = ord == 1 ? T(1) : ord == 2 ? T(3) : ord == 3 ? T(11) : T(25);
+    const T cl = (ord == 1 ? T(1) : ord == 2 ? T(2) : ord == 3 ? T(6) : T(12)) * a.dt;
     const T k0 = cl * a.delta[0], k1 = cl * a.delta[1];
     T* u = a.u;
     T* v = two ? a.v : nullptr;
@@ -237,12 +246,33 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
             T f, g;
             react(a, ui, vi, f, g);
             T bu, bv = T(0);
-            if (hist) {
+            if (ord == 2) {
                 bu = T(4) * ui - a.up[i] + T(2) * a.dt * (T(2) * f - a.fp[i]);
                 if (two) bv = T(4) * vi - a.vp[i] + T(2) * a.dt * (T(2) * g - a.gp[i]);
-            } else {
+            } else if (ord == 1) {
                 bu = ui + a.dt * f;
                 if (two) bv = vi + a.dt * g;
+            } else if (ord == 3) {
+                bu = (T(18) * ui - T(9) * a.up[i] + T(2) * a.up2[i]) +
+                     cl * (T(3) * f - T(3) * a.fp[i] + a.fp2[i]);
+                if (two)
+                    bv = (T(18) * vi - T(9) * a.vp[i] + T(2) * a.vp2[i]) +
+                         cl * (T(3) * g - T(3) * a.gp[i] + a.gp2[i]);
+            } else {
+                bu = (T(48) * ui - T(36) * a.up[i] + T(16) * a.up2[i] - T(3) * a.up3[i]) +
+                     cl * (T(4) * f - T(6) * a.fp[i] + T(4) * a.fp2[i] - a.fp3[i]);
+                if (two)
+                    bv = (T(48) * vi - T(36) * a.vp[i] + T(16) * a.vp2[i] - T(3) * a.vp3[i]) +
+                         cl * (T(4) * g - T(6) * a.gp[i] + T(4) * a.gp2[i] - a.gp3[i]);
+            }
+            // shift the history by one level (only the levels the order keeps)
+            if (a.order >= 4) {
+                a.up3[i] = a.up2[i];
+                a.fp3[i] = a.fp2[i];
+            }
+            if (a.order >= 3) {
+                a.up2[i] = a.up[i];
+                a.fp2[i] = a.fp[i];
             }
             a.up[i] = ui;
             a.fp[i] = f;
@@ -255,6 +285,14 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
             d[0] += (double)bu * bu;
             d[1] += (double)ru * ru;
             if (two) {
+                if (a.order >= 4) {
+                    a.vp3[i] = a.vp2[i];
+                    a.gp3[i] = a.gp2[i];
+                }
+                if (a.order >= 3) {
+                    a.vp2[i] = a.vp[i];
+                    a.gp2[i] = a.gp[i];
+                }
                 a.vp[i] = vi;
                 a.gp[i] = g;
                 T rv = bv - (c0 * vi - k1 * Lv);
@@ -469,7 +507,7 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
         a.rep_res[(int64_t)slot * 2] = relres[0];
         a.rep_res[(int64_t)slot * 2 + 1] = relres[1];
         if (bad) atomicExch(a.flags + 1, 1);
-        a.flags[2] = 1;          // history exists from now on
+        a.flags[2] = min(nhist + 1, max(a.order - 1, 1));   // past levels now stored
         a.flags[3] = slot + 1;   // every block read the slot before the first barrier
     }
 }
@@ -492,6 +530,15 @@ void fill_args(Args<T>& a, rbffd_op* op, rbffd_state* s, const rbffd_step_params
     a.vp = (T*)s->v_prev;
     a.fp = (T*)s->f_prev;
     a.gp = (T*)s->g_prev;
+    a.up2 = (T*)s->u_prev2;
+    a.vp2 = (T*)s->v_prev2;
+    a.fp2 = (T*)s->f_prev2;
+    a.gp2 = (T*)s->g_prev2;
+    a.up3 = (T*)s->u_prev3;
+    a.vp3 = (T*)s->v_prev3;
+    a.fp3 = (T*)s->f_prev3;
+    a.gp3 = (T*)s->g_prev3;
+    a.order = p->order == 0 ? 2 : p->order;
     a.vec = (T*)ws->vec;
     a.ns = p->nspecies;
     a.model = p->model;
@@ -571,6 +618,15 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
     RBFFD_CHECK_ARG(p->dt > 0 && p->tol > 0 && p->maxit > 0 && nsteps >= 0, "dt / tol / maxit / nsteps");
     RBFFD_CHECK_ARG(p->model >= RBFFD_MODEL_NONE && p->model <= RBFFD_MODEL_BARRIO, "model");
     RBFFD_CHECK_ARG(p->model != RBFFD_MODEL_BARRIO || p->coef[1] != 0.0, "Barrio model needs beta != 0");
+    const int order = p->order == 0 ? 2 : p->order;
+    RBFFD_CHECK_ARG(order >= 1 && order <= 4, "order must be 1..4 (0 = 2)");
+    RBFFD_CHECK_ARG(order < 3 || (s->u_prev2 && s->f_prev2 &&
+                                  (p->nspecies == 1 || (s->v_prev2 && s->g_prev2))),
+                    "SBDF3/4 need u_prev2 / f_prev2 (and v_prev2 / g_prev2)");
+    RBFFD_CHECK_ARG(order < 4 || (s->u_prev3 && s->f_prev3 &&
+                                  (p->nspecies == 1 || (s->v_prev3 && s->g_prev3))),
+                    "SBDF4 needs u_prev3 / f_prev3 (and v_prev3 / g_prev3)");
+    RBFFD_CHECK_ARG(s->has_history >= 0, "has_history must be >= 0");
     cudaStream_t st = as_stream(stream);
     const size_t elem = p->dtype == RBFFD_F32 ? 4 : 8;
     rbffd_step_ws* ws = op->step;
@@ -607,7 +663,8 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         RBFFD_CUDA_TRY(cudaMalloc(&ws->rep, ws->rep_cap * 3 * sizeof(int)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->rep_res, ws->rep_cap * 2 * sizeof(double)));
     }
-    int hflags[4] = {0, 0, s->has_history ? 1 : 0, 0};   // slot counter starts at 0
+    const int kept = std::max(order - 1, 1);   // past levels the order stores
+    int hflags[4] = {0, 0, std::min(s->has_history, kept), 0};   // slot counter starts at 0
     RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(ws->rep, 0, ws->rep_cap * 3 * sizeof(int), st));
     rbffd_status rs;
@@ -644,7 +701,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         r.last_relres_v = res[2 * k + 1];
     }
     r.steps_done = nsteps;
-    if (nsteps > 0) s->has_history = 1;
+    s->has_history = (int)std::min<int64_t>((int64_t)std::min(s->has_history, kept) + nsteps, kept);
     s->step += nsteps;
     if (report) *report = r;
     if (hflags[0]) {

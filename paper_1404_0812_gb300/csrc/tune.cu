@@ -109,8 +109,8 @@ extern "C" rbffd_status rbffd_autotune_build(const double* nodes, const double* 
     }
     // every candidate must see several stencils per lane, or the timing
     // measures the tail of the persistent loop instead of its throughput
-    const int cand_t[] = {64, 128, 128, 64};
-    const int cand_b[] = {4, 2, 3, 6};
+    const int cand_t[] = {128, 64, 128, 64};
+    const int cand_b[] = {4, 8, 3, 6};
     const int ncand = 4;
     int64_t max_lanes = 0;
     for (int c = 0; c < ncand; ++c) max_lanes = std::max<int64_t>(max_lanes, (int64_t)cand_t[c] * cand_b[c] * sm_count());

@@ -189,7 +189,7 @@ def test_autotune_picks_a_shape_and_caches_it(R, tmp_path):
     X, Nr, P = T(ns.X), T(ns.normals), T(nper, torch.int32)
     cache = tmp_path / "tune.txt"
     r = R.autotune_build(X, Nr, P, kernel="imq", sample=8000, cache_path=cache)
-    assert r["block_threads"] in (64, 128) and 1 <= r["blocks_per_sm"] <= 6 and r["ms"] > 0
+    assert r["block_threads"] in (64, 128) and 3 <= r["blocks_per_sm"] <= 8 and r["ms"] > 0
     r2 = R.autotune_build(X, Nr, P, kernel="imq", sample=8000, cache_path=cache)
     assert (r2["block_threads"], r2["blocks_per_sm"]) == (r["block_threads"], r["blocks_per_sm"])
     assert r2["ms"] == -1.0
@@ -200,3 +200,62 @@ def test_autotune_picks_a_shape_and_caches_it(R, tmp_path):
     ia, ib = R.get_stencil_info(a), R.get_stencil_info(b)
     assert torch.equal(ia["eps"], ib["eps"])
     assert torch.equal(R.get_rows(a)[1], R.get_rows(b)[1])
+
+
+def test_get_eps_and_ell_views(R):
+    """rbffd_get_eps equals the first three arrays of rbffd_get_stencil_info;
+    the borrowed sliced-ELL views, decoded with the documented element
+    formula, give exactly the rows of rbffd_get_rows."""
+    ns = W.fibonacci_sphere(2001)
+    nper = np.array([13, 31, 7])[np.arange(ns.N) % 3].astype(np.int32)
+    op = R.build_operator(T(ns.X), T(ns.normals), T(nper, torch.int32), kernel="imq", kappa_target=1e10)
+    eps, kappa, evals = R.get_eps(op)
+    info = R.get_stencil_info(op)
+    assert torch.equal(eps, info["eps"]) and torch.equal(kappa, info["kappa"])
+    assert torch.equal(evals, info["evals"])
+    v = R.get_ell(op)
+    assert v["ngroups"] == 3 and v["n"] == [31, 13, 7] and v["npad"] == [32, 16, 8]
+    idx = v["idx"].cpu().numpy()
+    w64 = v["w64"].cpu().numpy()
+    w32 = v["w32"].cpu().numpy()
+    row_node = v["row_node"].cpu().numpy()
+    assert sorted(row_node.tolist()) == list(range(ns.N))
+    ridx, rw = (t.cpu().numpy() for t in R.get_rows(op))
+    for g in range(v["ngroups"]):
+        n, npad, off = v["n"][g], v["npad"][g], v["elem_begin"][g]
+        for r in range(v["row_begin"][g], v["row_begin"][g + 1]):
+            q = r - v["row_begin"][g]
+            j = np.arange(npad)
+            e = off + (q // 32) * 32 * npad + (j // 4) * 128 + (q % 32) * 4 + j % 4
+            node = row_node[r]
+            assert nper[node] == n
+            assert np.array_equal(idx[e[:n]], ridx[node, :n])
+            assert np.array_equal(w64[e[:n]], rw[node, :n])
+            assert np.array_equal(w32[e[:n]], rw[node, :n].astype(np.float32))
+            assert np.all(w64[e[n:]] == 0.0) and np.all(idx[e[n:]] == node)
+    assert v["elems"] == v["elem_begin"][-1]
+
+
+def test_eps_search_range(R):
+    """A range that contains every root changes nothing beyond the search
+    tolerance; a range on the wrong side of the roots reports
+    RBFFD_STENCIL_NO_BRACKET for every stencil (build status
+    RBFFD_EPS_SEARCH_FAILED) instead of a wrong eps."""
+    ns = W.icosahedral_sphere(3)
+    X, Nr = T(ns.X), T(ns.normals)
+    free = R.build_operator(X, Nr, 31, kernel="imq", kappa_target=1e12)
+    e0 = R.get_stencil_info(free)["eps"].cpu().numpy()
+    inside = R.build_operator(X, Nr, 31, kernel="imq", kappa_target=1e12, eps_range=(1e-3, 1e3))
+    i1 = {k: t.cpu().numpy() for k, t in R.get_stencil_info(inside).items()}
+    assert np.all(i1["status"] == 0)
+    assert np.all(np.abs(i1["eps"] - e0) <= 2e-4 + 1e-5 * e0)
+    # kappa far above kappa_T (at eps * r_s = 1e-3 Phi does not even factor
+    # in float64: such a stencil reports SINGULAR) / far below it
+    for rng, allowed in (((1e-4, 1e-3), (1, 3)), ((1e3, 1e4), (1,))):
+        op = R.build_operator(X, Nr, 31, kernel="imq", kappa_target=1e12, eps_range=rng,
+                              allow_failures=True)
+        st = R.get_stencil_info(op)["status"].cpu().numpy()
+        assert op.status == 4 and np.all(np.isin(st, allowed))
+    with pytest.raises(R.RbffdError) as e:
+        R.build_operator(X, Nr, 31, eps_range=(2.0, 1.0))
+    assert e.value.status == 1

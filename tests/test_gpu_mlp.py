@@ -90,3 +90,17 @@ def test_training_reduces_loss_and_warm_start_saves_evaluations(R):
     assert np.all((il["kappa"][acc] >= 0.5e12) & (il["kappa"][acc] <= 2e12))
     assert np.all(np.abs(np.log(il["kappa"][~acc] / 1e12)) < 0.05)
     assert il["evals"].mean() < 0.6 * ip["evals"].mean()
+
+
+def test_mlp_load_replaces_parameters(R):
+    n = 31
+    p1 = W.mlp_pack(W.mlp_init(3 * n, seed=1)).astype(np.float32)
+    p2 = W.mlp_pack(W.mlp_init(3 * n, seed=2)).astype(np.float32)
+    a = R.EpsNet(n, p1)
+    a.load(p2)
+    assert np.array_equal(a.params(), p2)
+    b = R.EpsNet(n, p2)
+    x = T(np.random.default_rng(5).uniform(-1, 1, (100, 3 * n)), torch.float32)
+    assert torch.equal(a.predict(x), b.predict(x))
+    with pytest.raises(ValueError):
+        a.load(p2[:-1])

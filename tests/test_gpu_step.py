@@ -194,3 +194,62 @@ def test_graph_replay_matches_direct_launches(R):
         R.step_imex(op, st, p, 20)
         out.append((st.u.clone(), st.v.clone()))
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def test_bdf4_heat_exact_bootstrap_parity(R, sphere2562):
+    """Section 6's time stepping: BDF4 for the heat equation, the three past
+    levels taken from the exact solution exp(-12 t) Y_3^2; 100 steps of 1e-4
+    in float64 against the oracle's SBDF4 (<= 1e-9), at most three BiCGSTAB
+    iterations per step, and the same run in float32 (<= 1e-5)."""
+    ns, op, ref = sphere2562
+    dt = 1e-4
+    y = W.sph_harm_y32(ns.X)
+    levels = [math.exp(12 * dt * j) * y for j in (1, 2, 3)]
+    o = ostp.imex_run(lambda x: oop.apply(ref, x), y, None, dict(model="none", dt=dt, delta_u=1.0), 100,
+                      history=[(lv, None, np.zeros(ns.N), None) for lv in levels], order=4)
+    for dtype, tol, bound in ((torch.float64, 1e-12, 1e-9), (torch.float32, 1e-8, 1e-5)):
+        p = R.StepParams(model="none", nspecies=1, dtype=dtype, dt=dt, delta_u=1.0, tol=tol, order=4)
+        st = R.StepState.create(T(y, dtype), order=4)
+        st.u_prev.copy_(T(levels[0], dtype))
+        st.u_prev2.copy_(T(levels[1], dtype))
+        st.u_prev3.copy_(T(levels[2], dtype))
+        st.has_history = 3
+        rep = R.step_imex(op, st, p, 100)
+        assert rel_inf(st.u.cpu().numpy().astype(np.float64), o["u"]) <= bound
+        assert rep["max_iters_u"] <= 3 and st.has_history == 3
+    assert rel_inf(o["u"], math.exp(-12 * 0.01) * y) < 2e-5
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_sbdf_high_order_two_species_ramp(R, order):
+    """Two-species Schnakenberg (fixed-eps torus operator) from no history:
+    the first steps climb SBDF1, SBDF2, ... to the requested order, as the
+    oracle does; 30 steps in one call and as 7 + 23 (the state carries the
+    three past levels across calls); float64 parity <= 1e-9."""
+    ns = W.torus_staggered(20)
+    op, ref = _pair_fixed(R, ns, 31, "imq", 5.0)
+    s = W.SCHNAKENBERG
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    name, coef = R.model_coefs(s)
+    o = ostp.imex_run(lambda x: oop.apply(ref, x), u0, v0, s, 30, order=order)
+    for split in ((30,), (7, 23)):
+        p = R.StepParams(model=name, nspecies=2, dtype=torch.float64, dt=s["dt"], delta_u=s["delta_u"],
+                         delta_v=s["delta_v"], coef=coef, tol=1e-12, order=order, use_graph=True)
+        st = R.StepState.create(T(u0), T(v0), order=order)
+        for k in split:
+            R.step_imex(op, st, p, k)
+        assert st.has_history == order - 1 and st.step == 30
+        assert rel_inf(st.u.cpu().numpy(), o["u"]) <= 1e-9
+        assert rel_inf(st.v.cpu().numpy(), o["v"]) <= 1e-9
+
+
+def test_sbdf4_needs_its_history_buffers(R):
+    ns = W.icosahedral_sphere(1)
+    op = R.build_operator(T(ns.X), T(ns.normals), 10, kernel="imq", eps_override=T(np.full(ns.N, 2.0)))
+    st = R.StepState.create(T(W.sph_harm_y32(ns.X)), order=3)   # no level n-3
+    p = R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=1e-3, order=4)
+    with pytest.raises(R.RbffdError) as e:
+        R.step_imex(op, st, p, 1)
+    assert e.value.status == 1
+    with pytest.raises(R.RbffdError):
+        R.step_imex(op, st, R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=1e-3, order=5), 1)

@@ -107,3 +107,66 @@ def test_heat_equation_decay_and_iteration_count(op642):
     err = np.abs(out["u"] - math.exp(-12 * 0.01) * u0).max() / np.abs(u0).max()
     assert err < 2e-5
     assert max(i for i, _ in out["iters"]) <= g["max_iters"]
+
+
+def _scalar_run(order, lam, mu, dt, T):
+    """u' = -lam u + mu u (L = -I with delta = lam; f = mu u), u(0) = 1, the
+    order-1 past levels taken from the exact solution exp((mu - lam) t)."""
+    r = mu - lam
+    hist = [(np.array([math.exp(-r * dt * j)]), None, np.array([mu * math.exp(-r * dt * j)]), None)
+            for j in range(1, order)]
+    p = dict(model="linear", lu=mu, lv=0.0, dt=dt, delta_u=lam)
+    n = int(round(T / dt))
+    out = ostp.imex_run(lambda x: -x, np.array([1.0]), None, p, n, tol=1e-15, history=hist or None,
+                        order=order)
+    return abs(out["u"][0] - math.exp(r * n * dt))
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+def test_sbdf_order_of_accuracy(order):
+    """SBDFk is k-th order: with exact past levels, halving dt divides the
+    error at t = 1 by about 2^k -- separately for the implicit (diffusion)
+    and the explicit (kinetics) part, so every coefficient of both halves of
+    the scheme is pinned (a wrong one lowers the order)."""
+    for lam, mu in ((3.0, 0.0), (0.0, 1.5)):
+        e1 = _scalar_run(order, lam, mu, 0.02, 1.0)
+        e2 = _scalar_run(order, lam, mu, 0.01, 1.0)
+        rate = math.log2(e1 / e2)
+        assert abs(rate - order) < 0.25, (order, lam, mu, rate)
+
+
+def test_sbdf4_recurrence_closed_form():
+    """Scalar problem with L = -I: SBDF4 is the linear recurrence
+    u^{n+1} = sum_j c_j u^{n-j}; its solution is sum_i C_i z_i^n with z_i the
+    roots of the characteristic quartic (C from the four starting values)."""
+    lam, mu, dt = 4.0, 0.7, 0.03
+    alpha, a, b = 25.0 / 12.0, (4.0, -3.0, 4.0 / 3.0, -0.25), (4.0, -6.0, 4.0, -1.0)
+    c = [(a[j] + dt * mu * b[j]) / (alpha + dt * lam) for j in range(4)]
+    z = np.roots([1.0, -c[0], -c[1], -c[2], -c[3]])
+    start = np.array([1.0, 0.9, 0.83, 0.71])          # u^0, u^-1, u^-2, u^-3
+    V = np.array([[zi ** (-m) for zi in z] for m in range(4)])
+    C = np.linalg.solve(V, start.astype(complex))
+    n = 30
+    ref = float(np.real(np.sum(C * z ** n)))
+    hist = [(np.array([start[j]]), None, np.array([mu * start[j]]), None) for j in range(1, 4)]
+    p = dict(model="linear", lu=mu, lv=0.0, dt=dt, delta_u=lam)
+    out = ostp.imex_run(lambda x: -x, np.array([start[0]]), None, p, n, tol=1e-15, history=hist, order=4)
+    assert abs(out["u"][0] - ref) <= 1e-12 * abs(ref)
+
+
+def test_heat_equation_bdf4_exact_bootstrap(op642):
+    """Section 6's setting: BDF4 for the heat equation on the sphere started
+    from the exact solution (three past levels of exp(-12 t) Y_3^2); the
+    error at t = 0.01 is the spatial error of L_X (as for SBDF2) and BiCGSTAB
+    needs at most three iterations per step at dt = 1e-4."""
+    ns, op = op642
+    g = GOLDEN["bicgstab_bdf"]
+    dt = g["dt"]
+    y = W.sph_harm_y32(ns.X)
+    hist = [(math.exp(12 * dt * j) * y, None, np.zeros(ns.N), None) for j in range(1, 4)]
+    p = dict(model="none", dt=dt, delta_u=1.0)
+    out = ostp.imex_run(lambda x: oop.apply(op, x), y, None, p, 100, tol=g["tol"], history=hist, order=4)
+    err = np.abs(out["u"] - math.exp(-12 * 0.01) * y).max() / np.abs(y).max()
+    assert err < 2e-5
+    assert max(i for i, _ in out["iters"]) <= g["max_iters"]
+    assert len(out["levels"]) == 3
