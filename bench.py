@@ -54,7 +54,10 @@ METRIC = "stencils/s built at target kappa (batched mixed-n build + one IMEX ste
 UNIT = "stencils/s"
 # DRAM bytes per launch of the search kernel from one ncu capture, keyed by
 # the hash of build.cu at the time of the capture (None when not captured).
-SEARCH_TRAFFIC = {}
+# The capture ran the learned 160,000-node version of this workload (same four
+# stencil sizes, same networks): 233.26 GB read + 46.54 GB written; scaled to
+# the 1,000,000 stencils of one bench launch by the stencil count.
+SEARCH_TRAFFIC = {"3bab6ad6f53f6aa4": (233.26e9 + 46.54e9) * 1_000_000 / 160_000}
 
 
 def _parse():
@@ -241,13 +244,92 @@ def configs_report(R, W, T, torch, nets):
     its error instead of its numbers."""
     out = {}
     for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2), ("bumpy500k_learned", _c4),
-                     ("bumpy2m_pointcloud", _c5)):
+                     ("bumpy2m_pointcloud", _c5), ("sphere_heat_convergence_bdf4", _e3),
+                     ("sphere_heat_fixed_kappa_1e14", _e6)):
         try:
             out[name] = fn(R, W, T, torch, nets)
         except Exception as e:   # reported, not hidden
             out[name] = {"error": f"{type(e).__name__}: {e}"[:400]}
         torch.cuda.synchronize()
     return out
+
+
+def sphere_heat_study(R, W, T, torch, stencil_sizes=(11, 17, 31), levels=(3, 4, 5, 6), kappa="grow",
+                      dt=1e-3, t_end=0.5, kappa_cap=1e15):
+    """Section 6, diffusion on the sphere: u_t = Delta u from the 30-term
+    series of sectoral harmonics to t = 0.5 with BDF4 started from the exact
+    solution, on icosahedral nodes (N = 642 ... 40962), IMQ, float64.
+    kappa = "grow": kappa_T = 1e5 at the coarsest N, and at every finer N the
+    kappa_T (bisection in log kappa_T, capped at kappa_cap) that keeps the
+    mean shape parameter of the coarsest N (the paper's rule); a number: that
+    fixed kappa_T.  Returns per n the relative l2 / l_inf errors against the
+    exact solution and the observed orders in sqrt(N)."""
+    import numpy as np
+    res = {}
+    for n in stencil_sizes:
+        rows, eps_ref, kT_prev = [], None, 1e5
+        for lev in levels:
+            ns = W.icosahedral_sphere(lev)
+            X, Nr = T(ns.X), T(ns.normals)
+
+            def build(kT):
+                op = R.build_operator(X, Nr, n, kernel="imq", kappa_target=kT, allow_failures=True)
+                info = R.get_stencil_info(op)
+                return op, float(info["eps"].mean().item()), bool((info["status"] == 0).all().item())
+
+            capped = False
+            if kappa == "grow" and eps_ref is not None:
+                lo, hi = math.log(kT_prev), math.log(kappa_cap)
+                op, em, ok = build(kappa_cap)
+                if em > eps_ref:          # even kappa_cap keeps eps above the coarse mean
+                    kT, capped = kappa_cap, True
+                else:
+                    for _ in range(14):
+                        mid = 0.5 * (lo + hi)
+                        op, em, ok = build(math.exp(mid))
+                        if em > eps_ref:
+                            lo = mid
+                        else:
+                            hi = mid
+                    kT = math.exp(hi)
+                    op, em, ok = build(kT)
+            else:
+                kT = 1e5 if kappa == "grow" else float(kappa)
+                op, em, ok = build(kT)
+                if eps_ref is None:
+                    eps_ref = em
+            kT_prev = kT
+            t0 = 3 * dt
+            st = R.StepState.create(T(W.sphere_heat_series(ns.X, t0)), order=4)
+            st.u_prev.copy_(T(W.sphere_heat_series(ns.X, 2 * dt)))
+            st.u_prev2.copy_(T(W.sphere_heat_series(ns.X, dt)))
+            st.u_prev3.copy_(T(W.sphere_heat_series(ns.X, 0.0)))
+            st.has_history = 3
+            nsteps = int(round((t_end - t0) / dt))
+            p = R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=dt, delta_u=1.0, tol=1e-12,
+                             order=4, use_graph=True)
+            rep = R.step_imex(op, st, p, nsteps, allow_failure=True)
+            u = st.u.cpu().numpy()
+            ex = W.sphere_heat_series(ns.X, t0 + nsteps * dt)
+            rows.append({"N": ns.N, "kappa_T": float(f"{kT:.3g}"), "kappa_capped": capped,
+                         "eps_mean": round(em, 5), "stencils_ok": ok, "solver_status": rep["status"],
+                         "l2": float(f"{np.linalg.norm(u - ex) / np.linalg.norm(ex):.3e}"),
+                         "linf": float(f"{np.abs(u - ex).max() / np.abs(ex).max():.3e}")})
+            del op
+        for a, b in zip(rows, rows[1:]):
+            h = math.log(math.sqrt(b["N"] / a["N"]))
+            b["order_l2"] = round(math.log(a["l2"] / b["l2"]) / h, 2)
+            b["order_linf"] = round(math.log(a["linf"] / b["linf"]) / h, 2)
+        res[f"n{n}"] = rows
+    return res
+
+
+def _e3(R, W, T, torch, nets):
+    return sphere_heat_study(R, W, T, torch)
+
+
+def _e6(R, W, T, torch, nets):
+    return sphere_heat_study(R, W, T, torch, kappa=1e14)
 
 
 def _ev(torch):

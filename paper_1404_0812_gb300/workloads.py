@@ -217,6 +217,28 @@ def sph_harm_y32(X: np.ndarray) -> np.ndarray:
     return z * (x * x - y * y)
 
 
+def sectoral_harmonic(X: np.ndarray, l: int) -> np.ndarray:
+    """Real orthonormal sectoral spherical harmonic of degree and order l on
+    the unit sphere, Y_ll = c_l cos(lat)^l cos(l lon) = c_l Re((x + i y)^l),
+    c_l^2 = (2l+1)!! / (2 pi (2l)!!) (no Condon-Shortley sign).  A harmonic
+    homogeneous polynomial: Delta_S2 Y_ll = -l(l+1) Y_ll."""
+    c2 = 1.0 / (2.0 * np.pi)
+    for k in range(1, l + 1):
+        c2 *= (2.0 * k + 1.0) / (2.0 * k)
+    w = (X[:, 0] + 1j * X[:, 1]) ** l
+    return np.sqrt(c2) * w.real
+
+
+def sphere_heat_series(X: np.ndarray, t: float, terms: int = 30) -> np.ndarray:
+    """Section 6's heat-equation test on the unit sphere (from MacDonald and
+    Ruuth): u(t) = 20/(3 pi) sum_{l=1}^{terms} exp(-l^2/9) exp(-t l(l+1)) Y_ll,
+    the exact solution of u_t = Delta_S2 u, truncated after 30 terms."""
+    u = np.zeros(X.shape[0])
+    for l in range(1, terms + 1):
+        u += np.exp(-l * l / 9.0 - t * l * (l + 1)) * sectoral_harmonic(X, l)
+    return (20.0 / (3.0 * np.pi)) * u
+
+
 def stencil_size_groups(N: int, sizes=(31, 50, 70, 101)) -> np.ndarray:
     """Per-node stencil size for the mixed-n batched build: the node index
     range is cut into len(sizes) contiguous blocks of (nearly) equal length;

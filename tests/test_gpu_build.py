@@ -259,3 +259,38 @@ def test_eps_search_range(R):
     with pytest.raises(R.RbffdError) as e:
         R.build_operator(X, Nr, 31, eps_range=(2.0, 1.0))
     assert e.value.status == 1
+
+
+def test_largest_stencil_size(R):
+    """n = 128 (the largest the ABI accepts, m = 129): stencils bit-exact,
+    apply parity at fixed eps, and sampled searched eps against the oracle."""
+    ns = W.fibonacci_sphere(700)
+    n = 128
+    ref = oop.build_operator(ns.X, ns.normals, n, ow.IMQ, eps=np.full(ns.N, 1.5))
+    op = R.build_operator(T(ns.X), T(ns.normals), n, kernel="imq", eps_override=T(ref.eps))
+    idx, _ = R.get_rows(op)
+    assert np.array_equal(idx.cpu().numpy(), ref.idx.astype(np.int32))
+    u = W.sph_harm_y32(ns.X)
+    assert rel_inf(R.apply(op, T(u)).cpu().numpy(), oop.apply(ref, u)) <= 1e-8
+    op = R.build_operator(T(ns.X), T(ns.normals), n, kernel="imq", kappa_target=1e10)
+    info = {k: v.cpu().numpy() for k, v in R.get_stencil_info(op).items()}
+    assert np.all(info["status"] == 0)
+    for k in range(0, ns.N, 173):
+        e_ref, _, _ = ow.search_eps(ns.X[ref.idx[k]], ow.IMQ, 1e10)
+        assert abs(info["eps"][k] - e_ref) <= 2e-4 + 1e-5 * e_ref
+
+
+def test_degenerate_sizes_rejected(R):
+    ns = W.icosahedral_sphere(1)
+    X, Nr = T(ns.X), T(ns.normals)
+    for bad in (dict(n=129), dict(n=1)):
+        with pytest.raises(R.RbffdError) as e:
+            R.build_operator(X, Nr, bad["n"])
+        assert e.value.status == 1
+    with pytest.raises(R.RbffdError) as e:      # a single node has no stencil
+        R.build_operator(X[:1].contiguous(), Nr[:1].contiguous(), 2)
+    assert e.value.status == 1
+    nper = (np.arange(ns.N) % 9 + 2).astype(np.int32)   # nine distinct sizes > 8 groups
+    with pytest.raises(R.RbffdError) as e:
+        R.build_operator(X, Nr, T(nper, torch.int32))
+    assert e.value.status == 1

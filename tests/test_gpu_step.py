@@ -253,3 +253,21 @@ def test_sbdf4_needs_its_history_buffers(R):
     assert e.value.status == 1
     with pytest.raises(R.RbffdError):
         R.step_imex(op, st, R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=1e-3, order=5), 1)
+
+
+def test_sphere_heat_convergence_bdf4(R):
+    """Section 6, diffusion on the sphere: the 30-term series to t = 0.5 with
+    BDF4 from the exact solution, kappa_T = 1e5 at N = 642 and grown with N
+    so that the mean eps stays fixed; the observed orders in sqrt(N) are
+    those the section reports: between two and three for n = 11, close to
+    four for n = 17 (relative l2 error against the exact solution)."""
+    import bench
+    res = bench.sphere_heat_study(R, W, T, torch, stencil_sizes=(11, 17), levels=(3, 4, 5))
+    for rows in res.values():
+        assert all(r["stencils_ok"] and r["solver_status"] == 0 for r in rows)
+        e0 = rows[0]["eps_mean"]
+        assert all(abs(r["eps_mean"] / e0 - 1) < 1e-3 for r in rows)
+        assert rows[0]["kappa_T"] == 1e5 and rows[1]["kappa_T"] < rows[2]["kappa_T"]
+    assert 1.8 <= res["n11"][2]["order_l2"] <= 3.2
+    assert 3.3 <= res["n17"][2]["order_l2"] <= 4.7
+    assert res["n17"][2]["l2"] < 1e-3
