@@ -245,7 +245,8 @@ def configs_report(R, W, T, torch, nets):
     out = {}
     for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2), ("bumpy500k_learned", _c4),
                      ("bumpy2m_pointcloud", _c5), ("sphere_heat_convergence_bdf4", _e3),
-                     ("sphere_heat_fixed_kappa_1e14", _e6)):
+                     ("forced_sphere_convergence_bdf4", _e4), ("forced_torus_convergence_bdf4", _e5),
+                     ("forced_fixed_kappa_1e14", _e6)):
         try:
             out[name] = fn(R, W, T, torch, nets)
         except Exception as e:   # reported, not hidden
@@ -254,22 +255,35 @@ def configs_report(R, W, T, torch, nets):
     return out
 
 
-def sphere_heat_study(R, W, T, torch, stencil_sizes=(11, 17, 31), levels=(3, 4, 5, 6), kappa="grow",
-                      dt=1e-3, t_end=0.5, kappa_cap=1e15):
-    """Section 6, diffusion on the sphere: u_t = Delta u from the 30-term
-    series of sectoral harmonics to t = 0.5 with BDF4 started from the exact
-    solution, on icosahedral nodes (N = 642 ... 40962), IMQ, float64.
-    kappa = "grow": kappa_T = 1e5 at the coarsest N, and at every finer N the
-    kappa_T (bisection in log kappa_T, capped at kappa_cap) that keeps the
-    mean shape parameter of the coarsest N (the paper's rule); a number: that
-    fixed kappa_T.  Returns per n the relative l2 / l_inf errors against the
-    exact solution and the observed orders in sqrt(N)."""
+def convergence_study(R, W, T, torch, problem="heat_sphere", stencil_sizes=(11, 17, 31), sizes=None,
+                      kappa="grow", dt=None, t_end=None, kappa_cap=1e15):
+    """Section 6's convergence studies, IMQ, float64, BDF4 (order 4) started
+    from the exact solution at t = 0, dt, 2 dt:
+      heat_sphere    u_t = Delta u from the 30-term series of sectoral
+                     harmonics, to t = 0.5 (dt 1e-3), icosahedral N = 642..40962;
+      forced_sphere  u = exp(-5 t) sum_k exp(-10 theta_k^2), 23 centres, with
+                     its source taken implicitly, to t = 0.2 (dt 1e-4);
+      forced_torus   Eq. torus_forced (a = 9, b = 3), staggered N = 6 m^2,
+                     m = 10..80, to t = 0.2 (dt 1e-4).
+    kappa = "grow": kappa_T = 1e5 on the coarsest node set, and on every
+    finer one the kappa_T (bisection in log kappa_T, capped at kappa_cap) that
+    keeps the coarsest set's mean shape parameter; a number: that fixed
+    kappa_T.  Returns per n the relative l2 / l_inf errors against the exact
+    solution and the observed orders in sqrt(N)."""
     import numpy as np
+    torus = problem == "forced_torus"
+    if sizes is None:
+        sizes = (10, 20, 40, 80) if torus else (3, 4, 5, 6)
+    if dt is None:
+        dt = 1e-3 if problem == "heat_sphere" else 1e-4
+    if t_end is None:
+        t_end = 0.5 if problem == "heat_sphere" else 0.2
+    centers = W.torus_forced_centers() if torus else W.sphere_forced_centers()
     res = {}
     for n in stencil_sizes:
         rows, eps_ref, kT_prev = [], None, 1e5
-        for lev in levels:
-            ns = W.icosahedral_sphere(lev)
+        for size in sizes:
+            ns = W.torus_staggered(size) if torus else W.icosahedral_sphere(size)
             X, Nr = T(ns.X), T(ns.normals)
 
             def build(kT):
@@ -299,37 +313,59 @@ def sphere_heat_study(R, W, T, torch, stencil_sizes=(11, 17, 31), levels=(3, 4, 
                 if eps_ref is None:
                     eps_ref = em
             kT_prev = kT
+            if problem == "heat_sphere":
+                exact = lambda t: W.sphere_heat_series(ns.X, t)
+                src = None
+            else:
+                g, h = W.torus_forced(ns.X, centers) if torus else W.sphere_forced(ns.X, centers)
+                exact = lambda t: math.exp(-5.0 * t) * g
+                src = T(h)
             t0 = 3 * dt
-            st = R.StepState.create(T(W.sphere_heat_series(ns.X, t0)), order=4)
-            st.u_prev.copy_(T(W.sphere_heat_series(ns.X, 2 * dt)))
-            st.u_prev2.copy_(T(W.sphere_heat_series(ns.X, dt)))
-            st.u_prev3.copy_(T(W.sphere_heat_series(ns.X, 0.0)))
+            st = R.StepState.create(T(exact(t0)), order=4)
+            st.u_prev.copy_(T(exact(2 * dt)))
+            st.u_prev2.copy_(T(exact(dt)))
+            st.u_prev3.copy_(T(exact(0.0)))
             st.has_history = 3
+            st.t = t0
             nsteps = int(round((t_end - t0) / dt))
             p = R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=dt, delta_u=1.0, tol=1e-12,
-                             order=4, use_graph=True)
+                             order=4, use_graph=True, source_u=src, source_rate=-5.0)
             rep = R.step_imex(op, st, p, nsteps, allow_failure=True)
             u = st.u.cpu().numpy()
-            ex = W.sphere_heat_series(ns.X, t0 + nsteps * dt)
+            ex = exact(st.t)
             rows.append({"N": ns.N, "kappa_T": float(f"{kT:.3g}"), "kappa_capped": capped,
                          "eps_mean": round(em, 5), "stencils_ok": ok, "solver_status": rep["status"],
                          "l2": float(f"{np.linalg.norm(u - ex) / np.linalg.norm(ex):.3e}"),
                          "linf": float(f"{np.abs(u - ex).max() / np.abs(ex).max():.3e}")})
             del op
         for a, b in zip(rows, rows[1:]):
-            h = math.log(math.sqrt(b["N"] / a["N"]))
-            b["order_l2"] = round(math.log(a["l2"] / b["l2"]) / h, 2)
-            b["order_linf"] = round(math.log(a["linf"] / b["linf"]) / h, 2)
+            hN = math.log(math.sqrt(b["N"] / a["N"]))
+            b["order_l2"] = round(math.log(a["l2"] / b["l2"]) / hN, 2)
+            b["order_linf"] = round(math.log(a["linf"] / b["linf"]) / hN, 2)
         res[f"n{n}"] = rows
     return res
+
+
+def sphere_heat_study(R, W, T, torch, stencil_sizes=(11, 17, 31), levels=(3, 4, 5, 6), kappa="grow", **kw):
+    """The heat-equation study of Section 6 (see convergence_study)."""
+    return convergence_study(R, W, T, torch, "heat_sphere", stencil_sizes, levels, kappa, **kw)
 
 
 def _e3(R, W, T, torch, nets):
     return sphere_heat_study(R, W, T, torch)
 
 
+def _e4(R, W, T, torch, nets):
+    return convergence_study(R, W, T, torch, "forced_sphere")
+
+
+def _e5(R, W, T, torch, nets):
+    return convergence_study(R, W, T, torch, "forced_torus")
+
+
 def _e6(R, W, T, torch, nets):
-    return sphere_heat_study(R, W, T, torch, kappa=1e14)
+    return {"forced_sphere": convergence_study(R, W, T, torch, "forced_sphere", kappa=1e14),
+            "forced_torus": convergence_study(R, W, T, torch, "forced_torus", kappa=1e14)}
 
 
 def _ev(torch):

@@ -157,6 +157,10 @@ typedef struct {
     int use_graph;      /* 1: replay each step from a captured CUDA graph */
     int order;          /* SBDF order 1..4 (0 = 2, the SBDF2 of Section 7;
                            4 = the BDF4 of Section 6 with explicit kinetics) */
+    const void* source_u;   /* device, N values of dtype, or NULL: a forcing   */
+    const void* source_v;   /*   s(t, x) = exp(source_rate t) h(x) added to the */
+    double source_rate;     /*   species' equation and taken at t^{n+1}, i.e.   */
+                            /*   implicitly (Section 6's forced diffusion tests) */
 } rbffd_step_params;
 
 /*
@@ -178,6 +182,7 @@ typedef struct {
     int64_t step;       /* steps taken so far (updated) */
     void* u_prev2; void* v_prev2; void* f_prev2; void* g_prev2;
     void* u_prev3; void* v_prev3; void* f_prev3; void* g_prev3;
+    double t;           /* time of u (used by a source term; advanced by the call) */
 } rbffd_state;
 
 typedef struct {
@@ -197,7 +202,9 @@ typedef struct {
  *   (3 I - 2 dt delta L) u^{n+1} = 4 u^n - u^{n-1} + 2 dt (2 f^n - f^{n-1}),
  * and for k = 4
  *   (25 I - 12 dt delta L) u^{n+1} = 48 u^n - 36 u^{n-1} + 16 u^{n-2} - 3 u^{n-3}
- *                                    + 12 dt (4 f^n - 6 f^{n-1} + 4 f^{n-2} - f^{n-3}),
+ *                                    + 12 dt (4 f^n - 6 f^{n-1} + 4 f^{n-2} - f^{n-3})
+ *                                    + 12 dt s(t^{n+1})
+ * (s the optional source of params, zero without one),
  * each implicit system solved by BiCGSTAB from x0 = u^n (Section 4.2).
  * One cooperative persistent launch per step (optionally replayed from a
  * CUDA graph).  Synchronises the stream at the end and fills report (may be

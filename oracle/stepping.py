@@ -107,8 +107,12 @@ SBDF = {
 
 
 def imex_run(L_apply, u0, v0, p: dict, nsteps: int, tol: float = 1e-12,
-             maxit: int = 200, history=None, order: int = 2):
+             maxit: int = 200, history=None, order: int = 2, source=None, t0: float = 0.0):
     """Advance (u, v) by ``nsteps`` SBDF steps of the given order (1..4).
+
+    ``source`` = (rate, h_u, h_v) adds the forcing exp(rate t) h(x) to the
+    species' equations, taken at the new time t^{n+1} (implicitly, as Section
+    6 does for its forced diffusion tests); ``t0`` is the time of u0.
 
     ``L_apply(x)`` returns L_X x.  ``v0`` may be None for one species.
     ``history``: None, one past level (u_prev, v_prev, f_prev, g_prev), or a
@@ -140,6 +144,13 @@ def imex_run(L_apply, u0, v0, p: dict, nsteps: int, tol: float = 1e-12,
         past = [(u, v, f, g)] + levels[:k - 1]
         bu = sum(a[j] * past[j][0] for j in range(k)) + dt * sum(b[j] * past[j][2] for j in range(k))
         bv = sum(a[j] * past[j][1] for j in range(k)) + dt * sum(b[j] * past[j][3] for j in range(k))
+        if source is not None:
+            rate, hu, hv = source
+            amp = np.exp(rate * (t0 + (len(iters) + 1) * dt))
+            if hu is not None:
+                bu = bu + dt * amp * hu
+            if hv is not None:
+                bv = bv + dt * amp * hv
         c0, cl = alpha, dt
         Au = lambda x: c0 * x - (cl * du) * L_apply(x)
         un, iu, ru, oku = bicgstab(Au, bu, u, tol, maxit)
@@ -156,4 +167,4 @@ def imex_run(L_apply, u0, v0, p: dict, nsteps: int, tol: float = 1e-12,
         u, v = un, vn
         iters.append((iu, iv))
     return dict(u=u, v=v if two else None, history=levels[0] if levels else None, levels=levels,
-                iters=iters)
+                iters=iters, t=t0 + len(iters) * dt)

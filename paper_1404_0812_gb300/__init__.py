@@ -252,6 +252,9 @@ class StepParams:
     maxit: int = 200
     use_graph: bool = False
     order: int = 2          # SBDF order 1..4
+    source_u: torch.Tensor | None = None   # forcing exp(source_rate t) h(x), taken at t^{n+1}
+    source_v: torch.Tensor | None = None
+    source_rate: float = 0.0
 
 
 @dataclass
@@ -265,6 +268,7 @@ class StepState:
     g_prev: torch.Tensor | None = None
     has_history: int = 0
     step: int = 0
+    t: float = 0.0
     u_prev2: torch.Tensor | None = None
     v_prev2: torch.Tensor | None = None
     f_prev2: torch.Tensor | None = None
@@ -312,14 +316,20 @@ def step_imex(op: Operator, state: StepState, params: StepParams, nsteps: int, s
         sp.coef[i] = c
     sp.tol, sp.maxit, sp.use_graph = params.tol, params.maxit, int(params.use_graph)
     sp.order = int(params.order)
+    for name in ("source_u", "source_v"):
+        h = getattr(params, name)
+        if h is not None:
+            setattr(sp, name, _dev(h, params.dtype).data_ptr())
+    sp.source_rate = float(params.source_rate)
     cs = _lib.State(_ptr(state.u), _ptr(state.v), _ptr(state.u_prev), _ptr(state.v_prev),
                     _ptr(state.f_prev), _ptr(state.g_prev), state.has_history, state.step,
                     _ptr(state.u_prev2), _ptr(state.v_prev2), _ptr(state.f_prev2), _ptr(state.g_prev2),
-                    _ptr(state.u_prev3), _ptr(state.v_prev3), _ptr(state.f_prev3), _ptr(state.g_prev3))
+                    _ptr(state.u_prev3), _ptr(state.v_prev3), _ptr(state.f_prev3), _ptr(state.g_prev3),
+                    float(state.t))
     rep = _lib.StepReport()
     st = lib.rbffd_step_imex(op.handle, C.byref(cs), C.byref(sp), int(nsteps), _stream(stream),
                              C.byref(rep))
-    state.has_history, state.step = cs.has_history, cs.step
+    state.has_history, state.step, state.t = cs.has_history, cs.step, cs.t
     allow = (_lib.SOLVER_NOT_CONVERGED,) if allow_failure else ()
     _lib.check(st, "rbffd_step_imex", allow)
     return dict(status=st, steps_done=rep.steps_done, max_iters_u=rep.max_iters_u,

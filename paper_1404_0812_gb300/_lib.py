@@ -41,14 +41,15 @@ class EllView(C.Structure):
 class StepParams(C.Structure):
     _fields_ = [("model", C.c_int), ("nspecies", C.c_int), ("dtype", C.c_int), ("dt", C.c_double),
                 ("delta_u", C.c_double), ("delta_v", C.c_double), ("coef", C.c_double * 8),
-                ("tol", C.c_double), ("maxit", C.c_int), ("use_graph", C.c_int), ("order", C.c_int)]
+                ("tol", C.c_double), ("maxit", C.c_int), ("use_graph", C.c_int), ("order", C.c_int),
+                ("source_u", vp), ("source_v", vp), ("source_rate", C.c_double)]
 
 
 class State(C.Structure):
     _fields_ = [("u", vp), ("v", vp), ("u_prev", vp), ("v_prev", vp), ("f_prev", vp),
                 ("g_prev", vp), ("has_history", C.c_int), ("step", C.c_int64),
                 ("u_prev2", vp), ("v_prev2", vp), ("f_prev2", vp), ("g_prev2", vp),
-                ("u_prev3", vp), ("v_prev3", vp), ("f_prev3", vp), ("g_prev3", vp)]
+                ("u_prev3", vp), ("v_prev3", vp), ("f_prev3", vp), ("g_prev3", vp), ("t", C.c_double)]
 
 
 class StepReport(C.Structure):

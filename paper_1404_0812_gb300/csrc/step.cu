@@ -35,6 +35,7 @@ struct rbffd_step_ws {
                                    // [3] report slot of the next step
     int* rep;                      // per step: iters_u, iters_v, failed
     double* rep_res;               // per step: relres_u, relres_v
+    double* tstart;                // time of u at the start of the call (device copy)
     int64_t rep_cap;
     int blocks, threads;
     cudaGraphExec_t graph;            // captured step (memset + launch)
@@ -53,6 +54,7 @@ void step_ws_free(rbffd_step_ws* ws) {
     cudaFree(ws->flags);
     cudaFree(ws->rep);
     cudaFree(ws->rep_res);
+    cudaFree(ws->tstart);
     if (ws->graph) cudaGraphExecDestroy(ws->graph);
     if (ws->cap) cudaStreamDestroy(ws->cap);
     delete ws;
@@ -75,6 +77,9 @@ struct Args {
     T *up2, *vp2, *fp2, *gp2;   // levels n-2 and n-3 (SBDF3 / SBDF4 only)
     T *up3, *vp3, *fp3, *gp3;
     int order;         // SBDF order 1..4
+    const T *su, *sv;  // source profiles h_u, h_v (or NULL): s(t) = exp(rate t) h
+    double src_rate;
+    const double* tstart;   // time of u when the call began
     T* vec;            // 2 x 7 x N
     int ns;
     int model;
@@ -232,6 +237,8 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
     const T c0 = ord == 1 ? T(1) : ord == 2 ? T(3) : ord == 3 ? T(11) : T(25);
     const T cl = (ord == 1 ? T(1) : ord == 2 ? T(2) : ord == 3 ? T(6) : T(12)) * a.dt;
     const T k0 = cl * a.delta[0], k1 = cl * a.delta[1];
+    // the source is taken at the new time level t^{n+1} (implicitly)
+    const T samp = (a.su || a.sv) ? (T)exp(a.src_rate * (*a.tstart + (double)(slot + 1) * (double)a.dt)) : T(0);
     T* u = a.u;
     T* v = two ? a.v : nullptr;
 
@@ -265,6 +272,8 @@ __global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
                     bv = (T(48) * vi - T(36) * a.vp[i] + T(16) * a.vp2[i] - T(3) * a.vp3[i]) +
                          cl * (T(4) * g - T(6) * a.gp[i] + T(4) * a.gp2[i] - a.gp3[i]);
             }
+            if (a.su) bu += cl * samp * a.su[i];
+            if (two && a.sv) bv += cl * samp * a.sv[i];
             // shift the history by one level (only the levels the order keeps)
             if (a.order >= 4) {
                 a.up3[i] = a.up2[i];
@@ -539,6 +548,10 @@ void fill_args(Args<T>& a, rbffd_op* op, rbffd_state* s, const rbffd_step_params
     a.fp3 = (T*)s->f_prev3;
     a.gp3 = (T*)s->g_prev3;
     a.order = p->order == 0 ? 2 : p->order;
+    a.su = (const T*)p->source_u;
+    a.sv = p->nspecies == 2 ? (const T*)p->source_v : nullptr;
+    a.src_rate = p->source_rate;
+    a.tstart = ws->tstart;
     a.vec = (T*)ws->vec;
     a.ns = p->nspecies;
     a.model = p->model;
@@ -654,6 +667,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         RBFFD_CUDA_TRY(cudaMalloc(&ws->partial, (size_t)NPHASE * ws->blocks * NSLOT * sizeof(double)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->bar, sizeof(unsigned long long)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->flags, 4 * sizeof(int)));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->tstart, sizeof(double)));
         ws->rep_cap = 0;
     }
     if (ws->rep_cap < std::max<int64_t>(nsteps, 1)) {
@@ -666,6 +680,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
     const int kept = std::max(order - 1, 1);   // past levels the order stores
     int hflags[4] = {0, 0, std::min(s->has_history, kept), 0};   // slot counter starts at 0
     RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, st));
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->tstart, &s->t, sizeof(double), cudaMemcpyHostToDevice, st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(ws->rep, 0, ws->rep_cap * 3 * sizeof(int), st));
     rbffd_status rs;
     if (elem == 4) {
@@ -703,6 +718,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
     r.steps_done = nsteps;
     s->has_history = (int)std::min<int64_t>((int64_t)std::min(s->has_history, kept) + nsteps, kept);
     s->step += nsteps;
+    s->t += (double)nsteps * p->dt;
     if (report) *report = r;
     if (hflags[0]) {
         set_error("grid barrier timed out (blocks not co-resident?)");

@@ -239,6 +239,71 @@ def sphere_heat_series(X: np.ndarray, t: float, terms: int = 30) -> np.ndarray:
     return (20.0 / (3.0 * np.pi)) * u
 
 
+def sphere_forced_centers(K: int = 23, seed: int = 6) -> np.ndarray:
+    """K seeded uniformly random unit vectors (the centres xi_k of Section 6's
+    forced sphere problem)."""
+    v = np.random.default_rng(seed).normal(size=(K, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def sphere_forced(X: np.ndarray, centers: np.ndarray):
+    """Section 6's manufactured forced-diffusion solution on the unit sphere,
+    u(t, x) = exp(-5 t) g(x), g = sum_k exp(-10 theta_k^2), theta_k the
+    geodesic distance arccos(xi_k . x) (the exponent read as squared: the
+    printed exp(-10 theta_k) has a cusp at every centre, while the text calls
+    the solution smooth).  Returns (g, h) with h = -5 g - Delta_S2 g, so that
+    u_t = Delta u + exp(-5 t) h; for a zonal G(theta),
+    Delta G = G'' + cot(theta) G'."""
+    g = np.zeros(X.shape[0])
+    lap = np.zeros(X.shape[0])
+    for xi in centers:
+        c = np.clip(X @ xi, -1.0, 1.0)
+        th = np.arccos(c)
+        G = np.exp(-10.0 * th * th)
+        sn = np.sqrt(np.maximum(0.0, 1.0 - c * c))
+        # theta cot(theta) -> 1 at the centre; the antipode's G is ~1e-43
+        tcot = np.where(th < 1e-8, 1.0, np.where(sn > 1e-12, th * c / np.maximum(sn, 1e-300), 0.0))
+        g += G
+        lap += G * (-20.0 + 400.0 * th * th - 20.0 * tcot)
+    return g, -5.0 * g - lap
+
+
+def torus_angles(X: np.ndarray, R: float = 1.0):
+    """Intrinsic coordinates (phi, lambda) of points on the torus of Eq. torus."""
+    lam = np.arctan2(X[:, 1], X[:, 0])
+    rho = np.sqrt(X[:, 0] ** 2 + X[:, 1] ** 2) - R
+    return np.arctan2(X[:, 2], rho), lam
+
+
+def torus_forced_centers(K: int = 23, seed: int = 7) -> np.ndarray:
+    """(phi_k, lambda_k) uniformly random in [-pi, pi]^2 (seeded), K x 2."""
+    return np.random.default_rng(seed).uniform(-np.pi, np.pi, size=(K, 2))
+
+
+def torus_forced(X: np.ndarray, centers: np.ndarray, a: float = 9.0, b: float = 3.0):
+    """Section 6's manufactured forced-diffusion solution on the torus (Eq.
+    torus_forced): u = exp(-5 t) g, g = sum_k exp(-a^2 (1 - cos(lambda -
+    lambda_k)) - b^2 (1 - cos(phi - phi_k))).  Returns (g, h), h = -5 g -
+    Delta_M g with the intrinsic Laplacian of Section 6 (R = 1, r = 1/3):
+    Delta f = f_ll / rho^2 + 9 (rho'/rho f_p + f_pp), rho = 1 + cos(phi)/3."""
+    phi, lam = torus_angles(X)
+    rho = 1.0 + np.cos(phi) / 3.0
+    drho = -np.sin(phi) / 3.0
+    g = np.zeros(X.shape[0])
+    lap = np.zeros(X.shape[0])
+    for pk_, lk in centers:
+        L, P = lam - lk, phi - pk_
+        E = np.exp(-a * a * (1.0 - np.cos(L)) - b * b * (1.0 - np.cos(P)))
+        El = -a * a * np.sin(L) * E
+        Ell = (-a * a * np.cos(L) + a ** 4 * np.sin(L) ** 2) * E
+        Ep = -b * b * np.sin(P) * E
+        Epp = (-b * b * np.cos(P) + b ** 4 * np.sin(P) ** 2) * E
+        g += E
+        lap += Ell / rho ** 2 + 9.0 * (drho / rho * Ep + Epp)
+        del El
+    return g, -5.0 * g - lap
+
+
 def stencil_size_groups(N: int, sizes=(31, 50, 70, 101)) -> np.ndarray:
     """Per-node stencil size for the mixed-n batched build: the node index
     range is cut into len(sizes) contiguous blocks of (nearly) equal length;

@@ -271,3 +271,31 @@ def test_sphere_heat_convergence_bdf4(R):
     assert 1.8 <= res["n11"][2]["order_l2"] <= 3.2
     assert 3.3 <= res["n17"][2]["order_l2"] <= 4.7
     assert res["n17"][2]["l2"] < 1e-3
+
+
+def test_forced_sphere_bdf4_source_parity(R, sphere2562):
+    """Section 6's forced diffusion on the sphere (manufactured solution
+    exp(-5 t) g with its source exp(-5 t) h taken at t^{n+1}): BDF4 from the
+    exact solution, 40 steps of 1e-4 from t = 3e-4, float64 against the
+    oracle (<= 1e-9) and float32 (<= 1e-5); the state's time advances."""
+    ns, op, ref = sphere2562
+    dt = 1e-4
+    g, h = W.sphere_forced(ns.X, W.sphere_forced_centers())
+    ex = lambda t: math.exp(-5 * t) * g
+    o = ostp.imex_run(lambda x: oop.apply(ref, x), ex(3 * dt), None, dict(model="none", dt=dt, delta_u=1.0), 40,
+                      history=[(ex(2 * dt), None, np.zeros(ns.N), None), (ex(dt), None, np.zeros(ns.N), None),
+                               (ex(0.0), None, np.zeros(ns.N), None)],
+                      order=4, source=(-5.0, h, None), t0=3 * dt)
+    assert rel_inf(o["u"], ex(o["t"])) < 1e-3
+    for dtype, tol, bound in ((torch.float64, 1e-12, 1e-9), (torch.float32, 1e-8, 1e-5)):
+        p = R.StepParams(model="none", nspecies=1, dtype=dtype, dt=dt, delta_u=1.0, tol=tol, order=4,
+                         source_u=T(h, dtype), source_rate=-5.0, use_graph=True)
+        st = R.StepState.create(T(ex(3 * dt), dtype), order=4)
+        st.u_prev.copy_(T(ex(2 * dt), dtype))
+        st.u_prev2.copy_(T(ex(dt), dtype))
+        st.u_prev3.copy_(T(ex(0.0), dtype))
+        st.has_history, st.t = 3, 3 * dt
+        R.step_imex(op, st, p, 15)
+        R.step_imex(op, st, p, 25)        # the device time continues across calls
+        assert st.t == pytest.approx(3 * dt + 40 * dt)
+        assert rel_inf(st.u.cpu().numpy().astype(np.float64), o["u"]) <= bound

@@ -170,3 +170,23 @@ def test_heat_equation_bdf4_exact_bootstrap(op642):
     assert err < 2e-5
     assert max(i for i, _ in out["iters"]) <= g["max_iters"]
     assert len(out["levels"]) == 3
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+def test_implicit_source_keeps_order(order):
+    """u' = -lam u + exp(c t) h has the exact solution
+    u = (u0 - h/(c+lam)) exp(-lam t) + h exp(c t)/(c+lam); with exact past
+    levels SBDF-k keeps order k only if the source is taken at t^{n+1} (a
+    source at t^n would cost the scheme its order)."""
+    lam, c, h, T = 2.0, -1.0, 2.0, 1.0
+    exact = lambda t: (1.0 - h / (c + lam)) * math.exp(-lam * t) + h * math.exp(c * t) / (c + lam)
+    errs = []
+    for dt in (0.02, 0.01):
+        hist = [(np.array([exact(-dt * j)]), None, np.zeros(1), None) for j in range(1, order)]
+        p = dict(model="none", dt=dt, delta_u=lam)
+        n = int(round(T / dt))
+        out = ostp.imex_run(lambda x: -x, np.array([exact(0.0)]), None, p, n, tol=1e-15,
+                            history=hist or None, order=order, source=(c, np.array([h]), None))
+        assert out["t"] == pytest.approx(T)
+        errs.append(abs(out["u"][0] - exact(T)))
+    assert abs(math.log2(errs[0] / errs[1]) - order) < 0.3
