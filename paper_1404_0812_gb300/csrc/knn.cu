@@ -159,8 +159,11 @@ __device__ __forceinline__ double sq_dist(double ax, double ay, double az, doubl
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-__device__ __forceinline__ bool key_less(double da, int ia, double db, int ib) {
-    return da < db || (da == db && ia < ib);
+// (d^2, index) order.  d^2 >= +0 is never NaN, so its IEEE bit pattern read
+// as a signed 64-bit integer orders exactly as the double does; comparing the
+// integers keeps the insertion sort off the (slow) float64 pipe.
+__device__ __forceinline__ bool key_less(long long ka, int ia, long long kb, int ib) {
+    return ka < kb || (ka == kb && ia < ib);
 }
 
 // One thread per query, queries taken in cell-sorted order so that the 32
@@ -185,7 +188,7 @@ knn_query(const double* __restrict__ X, const int32_t* __restrict__ node_row, in
                  cell_coord(qz, g.lo[2], g.inv_h, g.G[2])};
     double qc[3] = {qx, qy, qz};
 
-    double bd[RBFFD_MAX_N];
+    long long bk[RBFFD_MAX_N];   // d^2 bit patterns of the current list
     int bi[RBFFD_MAX_N];
     int cnt = 0;
     int smax = max(g.G[0], max(g.G[1], g.G[2]));
@@ -216,17 +219,18 @@ knn_query(const double* __restrict__ X, const int32_t* __restrict__ node_row, in
                         if (j == q) continue;
                         double d2 = sq_dist(qx, qy, qz, sx[3 * (int64_t)p], sx[3 * (int64_t)p + 1],
                                             sx[3 * (int64_t)p + 2]);
-                        if (cnt == K && !key_less(d2, j, bd[K - 1], bi[K - 1])) continue;
+                        const long long kd = __double_as_longlong(d2);
+                        if (cnt == K && !key_less(kd, j, bk[K - 1], bi[K - 1])) continue;
                         int i = cnt < K ? cnt++ : K - 1;
-                        while (i > 0 && key_less(d2, j, bd[i - 1], bi[i - 1])) {
-                            bd[i] = bd[i - 1];
+                        while (i > 0 && key_less(kd, j, bk[i - 1], bi[i - 1])) {
+                            bk[i] = bk[i - 1];
                             bi[i] = bi[i - 1];
                             --i;
                         }
-                        bd[i] = d2;
+                        bk[i] = kd;
                         bi[i] = j;
                         if (cnt == K) {
-                            double kth = bd[K - 1];
+                            double kth = __longlong_as_double(bk[K - 1]);
                             kth_f = (float)(kth * (1.0 + 1e-6) + 4.0 * g.delta * sqrt(kth) +
                                             4.0 * g.delta * g.delta) * (1.0f + 1e-6f);
                         }
@@ -251,7 +255,7 @@ knn_query(const double* __restrict__ X, const int32_t* __restrict__ node_row, in
         if (all) break;
         if (cnt == K) {
             double b = bound * (1.0 - 1e-12);
-            if (b > 0.0 && bd[K - 1] < b * b) break;
+            if (b > 0.0 && __longlong_as_double(bk[K - 1]) < b * b) break;
         }
     }
     if (cnt < K) {

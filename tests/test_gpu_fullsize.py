@@ -1,0 +1,98 @@
+"""Parity at the benchmark's full size, in the configuration bench.py times:
+the 1,000,000-node Fibonacci sphere in four stencil-size bands (n = 31 / 50 /
+70 / 101), IMQ, kappa_T = 1e12, learned first guess (networks trained as the
+bench trains them), the bench's launch shape; then one float32 SBDF2 step of
+Schnakenberg on the built operator.  Sampled rows are checked against the
+oracle one by one; the step, a global solve, is checked by a property that
+holds at any size (its implicit equations are satisfied)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import stencils as ost
+from oracle import weights as ow
+from paper_1404_0812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SIZES = (31, 50, 70, 101)
+
+
+def T(a, dt=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1404_0812_gb300 as R
+    R._lib.load()
+    return R
+
+
+@pytest.fixture(scope="module")
+def built(R):
+    import bench
+    nets = bench.train_networks(R, W, T, torch)
+    ns = W.fibonacci_sphere(1_000_000)
+    nper = W.stencil_size_groups(ns.N, SIZES)
+    op = R.build_operator(T(ns.X), T(ns.normals), T(nper, torch.int32), kernel="imq", kappa_target=1e12,
+                          mlps=nets, block_threads=128, blocks_per_sm=4)
+    return ns, nper, op
+
+
+def test_learned_full_size_sampled_rows(R, built):
+    ns, nper, op = built
+    info = {k: v.cpu().numpy() for k, v in R.get_stencil_info(op).items()}
+    assert np.all((info["status"] == 0) | (info["status"] == 4))
+    assert (info["status"] == 4).mean() > 0.9          # the learned start carries the build
+    acc = info["status"] == 4
+    assert np.all((info["kappa"][acc] >= 0.5e12) & (info["kappa"][acc] <= 2e12))
+    assert np.all(np.abs(np.log(info["kappa"][~acc] / 1e12)) < 0.05)
+    idx, w = R.get_rows(op)
+    u = W.sph_harm_y32(ns.X)
+    y = R.apply(op, T(u)).cpu().numpy()
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([rng.choice(np.where(nper == n)[0], 5, replace=False) for n in SIZES])
+    rows = np.concatenate([rows, [0, ns.N - 1]])
+    sel = torch.as_tensor(rows, device="cuda")
+    idx_r, w_r = idx[sel].cpu().numpy(), w[sel].cpu().numpy()
+    for r, k in enumerate(rows):
+        n = int(nper[k])
+        sref = ost.stencil(ns.X, int(k), n)
+        assert np.array_equal(idx_r[r, :n], sref.astype(np.int32))
+        P = ns.X[sref]
+        kc = ow.cond2(ow.interp_matrix(P, info["eps"][k], ow.IMQ))
+        if info["status"][k] == 4:    # accepted prediction: inside the band by the oracle's kappa
+            assert 0.5e12 * 0.999 <= kc <= 2e12 * 1.001
+        assert abs(np.log(kc / info["kappa"][k])) < 1e-3
+        wref = ow.stencil_weights(P, ns.normals[sref], info["eps"][k], ow.IMQ)
+        assert np.abs(w_r[r, :n] - wref).max() <= 5e-4 * np.abs(wref).max()
+        # the applied operator at this row against the oracle's weights
+        assert abs(y[k] - wref @ u[sref]) <= 1e-8 * np.abs(wref).sum() * np.abs(u).max()
+
+
+@pytest.mark.parametrize("dtype,tol,bound", [(torch.float64, 1e-10, 1e-9), (torch.float32, 1e-6, 2e-5)])
+def test_full_size_step_satisfies_its_equations(R, built, dtype, tol, bound):
+    """One Schnakenberg step (IMEX Euler from no history) on the 1M operator:
+    the new state solves (I - dt delta L) u1 = u0 + dt f(u0), checked with the
+    apply of the same precision.  float64: to the solver's tolerance; float32
+    (the bench's stepping precision): to 2e-5, the solver's 1e-6 plus the
+    float32 rounding of a 101-term apply scaled by dt delta |L| ~ 10."""
+    ns, nper, op = built
+    s = W.SCHNAKENBERG
+    name, coef = R.model_coefs(s)
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    p = R.StepParams(model=name, nspecies=2, dtype=dtype, dt=s["dt"], delta_u=s["delta_u"],
+                     delta_v=s["delta_v"], coef=coef, tol=tol, use_graph=True)
+    st = R.StepState.create(T(u0, dtype), T(v0, dtype))
+    rep = R.step_imex(op, st, p, 1)
+    assert rep["status"] == 0
+    a, b, gam = s["a"], s["b"], s["gamma"]
+    f = gam * (a - u0 + u0 * u0 * v0)
+    g = gam * (b - u0 * u0 * v0)
+    for x1, x0, r0, d in ((st.u, u0, f, s["delta_u"]), (st.v, v0, g, s["delta_v"])):
+        Lx = R.apply(op, x1).double().cpu().numpy()
+        x = x1.double().cpu().numpy()
+        rhs = x0 + s["dt"] * r0
+        res = np.linalg.norm(x - s["dt"] * d * Lx - rhs) / np.linalg.norm(rhs)
+        assert res < bound, res
