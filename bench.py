@@ -256,7 +256,7 @@ def configs_report(R, W, T, torch, nets):
 
 
 def convergence_study(R, W, T, torch, problem="heat_sphere", stencil_sizes=(11, 17, 31), sizes=None,
-                      kappa="grow", dt=None, t_end=None, kappa_cap=1e15):
+                      kappa="grow", dt=None, t_end=None, f64_cap=1e15, dd_cap=1e24):
     """Section 6's convergence studies, IMQ, float64, BDF4 (order 4) started
     from the exact solution at t = 0, dt, 2 dt:
       heat_sphere    u_t = Delta u from the 30-term series of sectoral
@@ -266,10 +266,11 @@ def convergence_study(R, W, T, torch, problem="heat_sphere", stencil_sizes=(11, 
       forced_torus   Eq. torus_forced (a = 9, b = 3), staggered N = 6 m^2,
                      m = 10..80, to t = 0.2 (dt 1e-4).
     kappa = "grow": kappa_T = 1e5 on the coarsest node set, and on every
-    finer one the kappa_T (bisection in log kappa_T, capped at kappa_cap) that
-    keeps the coarsest set's mean shape parameter; a number: that fixed
-    kappa_T.  Returns per n the relative l2 / l_inf errors against the exact
-    solution and the observed orders in sqrt(N)."""
+    finer one the kappa_T that keeps the coarsest set's mean shape parameter
+    (regula falsi in log kappa_T); a number: that fixed kappa_T.  Builds with
+    kappa_T above f64_cap run in double-double (Section 6 computes those
+    weights in quad precision).  Returns per n the relative l2 / l_inf errors
+    against the exact solution and the observed orders in sqrt(N)."""
     import numpy as np
     torus = problem == "forced_torus"
     if sizes is None:
@@ -287,29 +288,47 @@ def convergence_study(R, W, T, torch, problem="heat_sphere", stencil_sizes=(11, 
             X, Nr = T(ns.X), T(ns.normals)
 
             def build(kT):
-                op = R.build_operator(X, Nr, n, kernel="imq", kappa_target=kT, allow_failures=True)
+                prec = "dd" if kT > f64_cap * 1.0001 else "f64"
+                op = R.build_operator(X, Nr, n, kernel="imq", kappa_target=kT, allow_failures=True,
+                                      precision=prec)
                 info = R.get_stencil_info(op)
-                return op, float(info["eps"].mean().item()), bool((info["status"] == 0).all().item())
+                return op, float(info["eps"].mean().item()), bool((info["status"] == 0).all().item()), prec
 
-            capped = False
             if kappa == "grow" and eps_ref is not None:
-                lo, hi = math.log(kT_prev), math.log(kappa_cap)
-                op, em, ok = build(kappa_cap)
-                if em > eps_ref:          # even kappa_cap keeps eps above the coarse mean
-                    kT, capped = kappa_cap, True
-                else:
-                    for _ in range(14):
-                        mid = 0.5 * (lo + hi)
-                        op, em, ok = build(math.exp(mid))
-                        if em > eps_ref:
-                            lo = mid
-                        else:
-                            hi = mid
-                    kT = math.exp(hi)
-                    op, em, ok = build(kT)
+                # g(y) = ln(mean eps(kappa_T = e^y) / eps_ref) decreases in y:
+                # bracket it (float64 up to f64_cap, double-double beyond),
+                # then Illinois regula falsi to |g| < 1e-4
+                def g(y):
+                    r = build(math.exp(y))
+                    return math.log(r[1] / eps_ref), r
+
+                a = math.log(kT_prev)
+                ga, ra = g(a)
+                b = math.log(f64_cap)
+                gb, rb = g(b)
+                if gb > 0:
+                    a, ga, ra = b, gb, rb
+                    b = math.log(dd_cap)
+                    gb, rb = g(b)
+                y, gy, ry = (a, ga, ra) if abs(ga) < abs(gb) else (b, gb, rb)
+                side = 0
+                for _ in range(20):
+                    if abs(gy) < 1e-4 or ga * gb > 0:
+                        break
+                    y = b - gb * (b - a) / (gb - ga)
+                    gy, ry = g(y)
+                    if gy * gb < 0:
+                        a, ga, ra = b, gb, rb
+                        side = 0
+                    else:
+                        ga = 0.5 * ga if side == 1 else ga
+                        side = 1
+                    b, gb, rb = y, gy, ry
+                kT = math.exp(y)
+                op, em, ok, prec = ry
             else:
                 kT = 1e5 if kappa == "grow" else float(kappa)
-                op, em, ok = build(kT)
+                op, em, ok, prec = build(kT)
                 if eps_ref is None:
                     eps_ref = em
             kT_prev = kT
@@ -333,7 +352,7 @@ def convergence_study(R, W, T, torch, problem="heat_sphere", stencil_sizes=(11, 
             rep = R.step_imex(op, st, p, nsteps, allow_failure=True)
             u = st.u.cpu().numpy()
             ex = exact(st.t)
-            rows.append({"N": ns.N, "kappa_T": float(f"{kT:.3g}"), "kappa_capped": capped,
+            rows.append({"N": ns.N, "kappa_T": float(f"{kT:.3g}"), "precision": prec,
                          "eps_mean": round(em, 5), "stencils_ok": ok, "solver_status": rep["status"],
                          "l2": float(f"{np.linalg.norm(u - ex) / np.linalg.norm(ex):.3e}"),
                          "linf": float(f"{np.abs(u - ex).max() / np.abs(ex).max():.3e}")})

@@ -47,6 +47,7 @@ typedef enum {
 
 enum { RBFFD_GAUSSIAN = 0, RBFFD_IMQ = 1 };   /* Section 2 kernels */
 enum { RBFFD_F32 = 0, RBFFD_F64 = 1 };        /* stepping / apply precision */
+enum { RBFFD_PREC_F64 = 0, RBFFD_PREC_DD = 1 }; /* arithmetic of the operator build */
 enum { RBFFD_MAX_GROUPS = 8, RBFFD_MAX_N = 128 };
 
 /* Per-stencil status codes written by the build (rbffd_get_stencil_info). */
@@ -76,6 +77,14 @@ typedef struct {
     double eps_hi;            /*   (r_s = the stencil's largest centre distance);
                                  0 = unbounded on that side.  A stencil whose
                                  root lies outside gets RBFFD_STENCIL_NO_BRACKET */
+    int precision;            /* RBFFD_PREC_F64 (default) or RBFFD_PREC_DD: the
+                                 geometry, Phi, its factorisation, the A^{-1}
+                                 solves and the weights in double-double
+                                 arithmetic (unit roundoff ~1e-32) for kappa_T
+                                 beyond float64 (Section 6 uses quad precision
+                                 for kappa_T = 1e18 / 1e20); the weights are
+                                 rounded to float64.  Much slower; the launch
+                                 shape fields are ignored. */
 } rbffd_build_opts;
 
 /* Fill opts with defaults: IMQ, kappa_T 1e12, eps_tol 1e-4, max_evals 64,

@@ -66,10 +66,11 @@ class Operator:
 def build_operator(nodes, normals, n=31, kernel="imq", kappa_target=1e12, eps_tol=1e-4,
                    max_evals=64, eps_override=None, mlps=None, accept=(0.5, 2.0),
                    block_threads=0, blocks_per_sm=0, stream=None, allow_failures=False,
-                   eps_range=(0.0, 0.0)):
+                   eps_range=(0.0, 0.0), precision="f64"):
     """rbffd_build_operator.  ``n`` is an int or a CUDA int32 tensor (N,);
     ``mlps`` a list of EpsNet to warm-start the search; ``eps_range`` the
-    search range of eps * r_s (0 = unbounded on that side)."""
+    search range of eps * r_s (0 = unbounded on that side); ``precision``
+    "f64" or "dd" (double-double, for kappa_T beyond float64)."""
     lib = _lib.load()
     nodes = _dev(nodes, torch.float64)
     normals = _dev(normals, torch.float64)
@@ -90,6 +91,7 @@ def build_operator(nodes, normals, n=31, kernel="imq", kappa_target=1e12, eps_to
             o.mlp[i] = m.handle
     o.block_threads, o.blocks_per_sm = int(block_threads), int(blocks_per_sm)
     o.eps_lo, o.eps_hi = float(eps_range[0]), float(eps_range[1])
+    o.precision = {"f64": _lib.PREC_F64, "dd": _lib.PREC_DD}[precision]
     if isinstance(n, torch.Tensor):
         npn = _dev(n, torch.int32)
         nptr, nu = C.c_void_p(npn.data_ptr()), 0

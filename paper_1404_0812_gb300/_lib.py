@@ -16,6 +16,7 @@ RBFFD_MAX_GROUPS = 8
 OK, EINVAL, ECUDA, ENOMEM, EPS_SEARCH_FAILED, SOLVER_NOT_CONVERGED, TIMEOUT, NOT_IMPLEMENTED, ESINGULAR = range(9)
 GAUSSIAN, IMQ = 0, 1
 F32, F64 = 0, 1
+PREC_F64, PREC_DD = 0, 1
 MODEL_NONE, MODEL_LINEAR, MODEL_SCHNAKENBERG, MODEL_GRAY_SCOTT, MODEL_BARRIO = range(5)
 STENCIL_OK, STENCIL_NO_BRACKET, STENCIL_NO_CONVERGENCE, STENCIL_SINGULAR, STENCIL_ACCEPTED_PREDICTION = range(5)
 
@@ -27,7 +28,8 @@ class BuildOpts(C.Structure):
                 ("max_evals", C.c_int), ("use_learned", C.c_int), ("accept_lo", C.c_double),
                 ("accept_hi", C.c_double), ("eps_override", vp),
                 ("mlp", vp * RBFFD_MAX_GROUPS), ("block_threads", C.c_int),
-                ("blocks_per_sm", C.c_int), ("eps_lo", C.c_double), ("eps_hi", C.c_double)]
+                ("blocks_per_sm", C.c_int), ("eps_lo", C.c_double), ("eps_hi", C.c_double),
+                ("precision", C.c_int)]
 
 
 class EllView(C.Structure):

@@ -148,6 +148,7 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     RBFFD_CHECK_ARG(o.eps_lo >= 0.0 && o.eps_hi >= 0.0 && std::isfinite(o.eps_lo) && std::isfinite(o.eps_hi),
                     "eps_lo / eps_hi must be finite and >= 0");
     RBFFD_CHECK_ARG(o.eps_lo == 0.0 || o.eps_hi == 0.0 || o.eps_lo < o.eps_hi, "eps_lo must be < eps_hi");
+    RBFFD_CHECK_ARG(o.precision == RBFFD_PREC_F64 || o.precision == RBFFD_PREC_DD, "precision");
     cudaStream_t st = as_stream(stream);
 
     // ---- stencil-size groups (sorted by descending n; stable node order)
@@ -262,7 +263,8 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
             }
         }
         TRY_OP(cudaEventRecord(ev[2], st));
-        s = build_search(op, nodes, normals, o, guess, st);
+        s = o.precision == RBFFD_PREC_DD ? build_search_dd(op, nodes, normals, o, guess, nullptr, st)
+                                         : build_search(op, nodes, normals, o, guess, st);
         TRY_OP(cudaEventRecord(ev[3], st));
         TRY_OP(cudaEventRecord(ev[4], st));   // no separate weights phase
         if (guess) cudaFreeAsync(guess, st);
@@ -287,7 +289,25 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     }
     // ---- weights (the search writes them itself from its last factorisation)
     if (o.eps_override) {
-        s = build_weights(op, nodes, normals, o, op->eps, st);
+        if (o.precision == RBFFD_PREC_DD) {
+            s = build_search_dd(op, nodes, normals, o, nullptr, op->eps, st);
+            if (s != RBFFD_OK) return fail(s);
+            int* bad = nullptr;
+            TRY_OP(cudaMallocAsync(&bad, sizeof(int), st));
+            TRY_OP(cudaMemsetAsync(bad, 0, sizeof(int), st));
+            count_status<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->status, N, bad);
+            note_launch();
+            int hb = 0;
+            TRY_OP(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TRY_OP(cudaStreamSynchronize(st));
+            cudaFreeAsync(bad, st);
+            if (hb) {
+                set_error("%d stencils have a local matrix that is not numerically positive definite", hb);
+                s = RBFFD_ESINGULAR;
+            }
+        } else {
+            s = build_weights(op, nodes, normals, o, op->eps, st);
+        }
         if (s != RBFFD_OK && s != RBFFD_ESINGULAR) return fail(s);
         TRY_OP(cudaEventRecord(ev[4], st));
     } else {

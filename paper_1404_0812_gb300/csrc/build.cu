@@ -41,6 +41,7 @@
 // four solves and one pass over the pairs, equal in exact arithmetic to
 // forming the full G^d (which the oracle does).
 #include "common.cuh"
+#include "dd.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -1440,3 +1441,559 @@ extern "C" rbffd_status rbffd_stencil_weights_noalloc(const double* nodes, const
     }
     return RBFFD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Double-double build (rbffd_build_opts.precision = RBFFD_PREC_DD): the same
+// search and weights with every step that the condition number amplifies --
+// geometry, Phi, its Cholesky factor, the A^{-1} solves, the weights -- in
+// double-double arithmetic (unit roundoff ~1e-32), for target condition
+// numbers beyond float64 (Section 6 computes its kappa_T = 1e18 / 1e20
+// weights in quad precision and then rounds them to float64, as this path
+// does).  The A Lanczos run (lambda_max, well conditioned), the tridiagonal
+// eigenvalues and the Hellmann-Feynman slope stay in float64 / float32.
+// Plain loops: these builds are for the high-kappa studies, not for speed.
+// ---------------------------------------------------------------------------
+namespace rbffd {
+namespace {
+
+// lane-interleaved storage of double-double elements: element e of a lane
+// occupies float64 slots 2e (hi) and 2e + 1 (lo) of that lane
+struct LaneDD {
+    double* p;
+    __device__ __forceinline__ dd get(int e) const {
+        return dd{p[(int64_t)(2 * e) * 32], p[(int64_t)(2 * e + 1) * 32]};
+    }
+    __device__ __forceinline__ void set(int e, dd v) const {
+        p[(int64_t)(2 * e) * 32] = v.hi;
+        p[(int64_t)(2 * e + 1) * 32] = v.lo;
+    }
+    __device__ __forceinline__ double hi(int e) const { return p[(int64_t)(2 * e) * 32]; }
+};
+
+struct LayoutDD {
+    int m, P;
+    int XS, NS, R2, L, PH, U, ID, V0, V1, V2, QB, RV, GV, HV;
+    int size;   // double-double elements per lane
+};
+
+__host__ __device__ inline LayoutDD make_layout_dd(int m) {
+    LayoutDD l;
+    l.m = m;
+    l.P = m * (m + 1) / 2;
+    int o = 0;
+    l.XS = o; o += 3 * m;
+    l.NS = o; o += 3 * m;
+    l.R2 = o; o += l.P;
+    l.L = o; o += l.P;
+    l.PH = o; o += l.P;
+    l.U = o; o += m;
+    l.ID = o; o += m;
+    l.V0 = o; o += m;
+    l.V1 = o; o += m;
+    l.V2 = o; o += m;
+    l.QB = o; o += LANCZOS_KMAX * m;
+    l.RV = o; o += m;
+    l.GV = o; o += 3 * m;
+    l.HV = o; o += 3 * m;
+    l.size = o;
+    return l;
+}
+
+// centre-translated (exact differences), r_s-scaled coordinates, unit
+// normals and pairwise squared distances, all in double-double
+__device__ Geo geometry_dd(const LaneDD& S, const LayoutDD& ly, int n, const int32_t* __restrict__ idx,
+                           int64_t off, int npad, int64_t lr, const double* __restrict__ X,
+                           const double* __restrict__ NR) {
+    const int m = ly.m;
+    int c = idx[ell_elem(off, npad, lr, 0)];
+    const double cx = X[3 * (int64_t)c], cy = X[3 * (int64_t)c + 1], cz = X[3 * (int64_t)c + 2];
+    double rs2 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        int k = idx[ell_elem(off, npad, lr, j)];
+        dd d0 = two_sum(X[3 * (int64_t)k], -cx), d1 = two_sum(X[3 * (int64_t)k + 1], -cy),
+           d2 = two_sum(X[3 * (int64_t)k + 2], -cz);
+        S.set(ly.XS + j, d0);
+        S.set(ly.XS + m + j, d1);
+        S.set(ly.XS + 2 * m + j, d2);
+        rs2 = fmax(rs2, d0.hi * d0.hi + d1.hi * d1.hi + d2.hi * d2.hi);
+        double nx = NR[3 * (int64_t)k], ny = NR[3 * (int64_t)k + 1], nz = NR[3 * (int64_t)k + 2];
+        double inv = rsqrt(nx * nx + ny * ny + nz * nz);
+        S.set(ly.NS + j, dd_of(nx * inv));
+        S.set(ly.NS + m + j, dd_of(ny * inv));
+        S.set(ly.NS + 2 * m + j, dd_of(nz * inv));
+    }
+    Geo g;
+    g.rs = sqrt(rs2);
+    const double inv = 1.0 / g.rs;
+    double sum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        dd x = S.get(ly.XS + j) * inv, y = S.get(ly.XS + m + j) * inv, z = S.get(ly.XS + 2 * m + j) * inv;
+        S.set(ly.XS + j, x);
+        S.set(ly.XS + m + j, y);
+        S.set(ly.XS + 2 * m + j, z);
+        if (j > 0) sum += sqrt(x.hi * x.hi + y.hi * y.hi + z.hi * z.hi);
+    }
+    g.mean_d = sum / (double)(n - 1);
+    for (int i = 0; i < n; ++i) {
+        const dd xi = S.get(ly.XS + i), yi = S.get(ly.XS + m + i), zi = S.get(ly.XS + 2 * m + i);
+        for (int j = 0; j < i; ++j) {
+            dd dx = xi - S.get(ly.XS + j), dy = yi - S.get(ly.XS + m + j), dz = zi - S.get(ly.XS + 2 * m + j);
+            S.set(ly.R2 + pk(i, j), dx * dx + dy * dy + dz * dz);
+        }
+        S.set(ly.R2 + pk(i, i), dd_of(0.0));
+    }
+    return g;
+}
+
+__device__ __forceinline__ dd phi_dd(int kernel, dd e2r2) {
+    return kernel == RBFFD_GAUSSIAN ? dd_exp(-e2r2) : dd_of(1.0) / dd_sqrt(dd_of(1.0) + e2r2);
+}
+__device__ __forceinline__ dd psi_from_phi_dd(int kernel, dd e2, dd ph) {
+    return kernel == RBFFD_GAUSSIAN ? -(e2 * ph * 2.0) : -(e2 * ph * ph * ph);
+}
+
+// Phi(eps_s) into L and PH (packed lower, identity on the padding)
+__device__ void assemble_dd(const LaneDD& S, const LayoutDD& ly, int n, int kernel, double eps_s) {
+    const dd e2 = two_prod(eps_s, eps_s);
+    for (int i = 0; i < ly.m; ++i) {
+        for (int j = 0; j < i; ++j) {
+            dd v = i < n ? phi_dd(kernel, e2 * S.get(ly.R2 + pk(i, j))) : dd_of(0.0);
+            S.set(ly.L + pk(i, j), v);
+            S.set(ly.PH + pk(i, j), v);
+        }
+        S.set(ly.L + pk(i, i), dd_of(1.0));
+        S.set(ly.PH + pk(i, i), dd_of(1.0));
+    }
+}
+
+// in-place packed Cholesky, L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj;
+// ID receives 1 / L_jj.  false when a pivot is not positive.
+__device__ bool cholesky_dd(const LaneDD& S, const LayoutDD& ly) {
+    const int m = ly.m;
+    for (int j = 0; j < m; ++j) {
+        dd d = S.get(ly.L + pk(j, j));
+        for (int k = 0; k < j; ++k) {
+            dd l = S.get(ly.L + pk(j, k));
+            d = fms(d, l, l);
+        }
+        if (!(d.hi > 0.0)) return false;
+        dd ljj = dd_sqrt(d);
+        dd il = dd_of(1.0) / ljj;
+        S.set(ly.L + pk(j, j), ljj);
+        S.set(ly.ID + j, il);
+        for (int i = j + 1; i < m; ++i) {
+            dd s = S.get(ly.L + pk(i, j));
+            for (int k = 0; k < j; ++k) s = fms(s, S.get(ly.L + pk(i, k)), S.get(ly.L + pk(j, k)));
+            S.set(ly.L + pk(i, j), s * il);
+        }
+    }
+    return true;
+}
+
+// V <- Phi^{-1} V
+__device__ void chol_solve_dd(const LaneDD& S, const LayoutDD& ly, int V) {
+    const int m = ly.m;
+    for (int i = 0; i < m; ++i) {
+        dd t = S.get(V + i);
+        for (int k = 0; k < i; ++k) t = fms(t, S.get(ly.L + pk(i, k)), S.get(V + k));
+        S.set(V + i, t * S.get(ly.ID + i));
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        dd t = S.get(V + i);
+        for (int k = i + 1; k < m; ++k) t = fms(t, S.get(ly.L + pk(k, i)), S.get(V + k));
+        S.set(V + i, t * S.get(ly.ID + i));
+    }
+}
+
+// [c; d] = A^{-1} [f; g] with c in V (first n entries), d returned:
+// c0 = Phi^{-1} f, d = (1^T c0 - g) / s, c = c0 - d u
+__device__ dd aug_solve_dd(const LaneDD& S, const LayoutDD& ly, int n, int V, dd g, dd s) {
+    chol_solve_dd(S, ly, V);
+    dd sum = dd_of(0.0);
+    for (int i = 0; i < n; ++i) sum = sum + S.get(V + i);
+    dd d = (sum - g) / s;
+    for (int i = 0; i < n; ++i) S.set(V + i, fms(S.get(V + i), d, S.get(ly.U + i)));
+    return d;
+}
+
+// Lanczos on A^{-1} from the stencil's pseudo-random start (as the float64
+// search does): returns the Ritz value of largest magnitude and leaves the
+// Ritz vector (float64 values as hi parts) in RV with its border in *vb.
+__device__ double lanczos_inv_dd(const LaneDD& S, const LayoutDD& ly, int n, dd s, uint64_t seed, double* vb) {
+    const int m = ly.m;
+    float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
+    double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX];
+    dd qbord[LANCZOS_KMAX + 1];
+    dd nrm2 = dd_of(0.0);
+    for (int i = 0; i < m; ++i) {
+        dd v = dd_of(i < n ? unit_hash(seed * 131u + i) : 0.0);
+        S.set(ly.QB + i, v);
+        nrm2 = nrm2 + v * v;
+    }
+    dd qb = dd_of(unit_hash(seed * 131u + n));
+    nrm2 = nrm2 + qb * qb;
+    dd inrm = dd_of(1.0) / dd_sqrt(nrm2);
+    for (int i = 0; i < n; ++i) S.set(ly.QB + i, S.get(ly.QB + i) * inrm);
+    qbord[0] = qb * inrm;
+    dd beta = dd_of(0.0);
+    double prev = -1.0, ext = 0.0;
+    int k = 0;
+    for (int j = 0; j < LANCZOS_KMAX; ++j) {
+        const int qj = ly.QB + j * m, qp = ly.QB + (j - 1) * m;
+        for (int i = 0; i < m; ++i) S.set(ly.V0 + i, S.get(qj + i));
+        dd wb = aug_solve_dd(S, ly, n, ly.V0, qbord[j], s);
+        if (j > 0) {
+            for (int i = 0; i < m; ++i) S.set(ly.V0 + i, fms(S.get(ly.V0 + i), beta, S.get(qp + i)));
+            wb = fms(wb, beta, qbord[j - 1]);
+        }
+        dd a = qbord[j] * wb;
+        for (int i = 0; i < m; ++i) a = a + S.get(qj + i) * S.get(ly.V0 + i);
+        dd bn2 = dd_of(0.0);
+        for (int i = 0; i < m; ++i) {
+            dd v = fms(S.get(ly.V0 + i), a, S.get(qj + i));
+            S.set(ly.V0 + i, v);
+            bn2 = bn2 + v * v;
+        }
+        wb = fms(wb, a, qbord[j]);
+        bn2 = bn2 + wb * wb;
+        dd bn = dd_sqrt(bn2);
+        alpha_d[j] = a.hi;
+        beta_d[j] = bn.hi;
+        k = j + 1;
+        double G = 0.0;
+        for (int i = 0; i <= j; ++i)
+            G = fmax(G, fabs(alpha_d[i]) + (i < j ? beta_d[i] : 0.0) + (i > 0 ? beta_d[i - 1] : 0.0));
+        const double ig = 1.0 / G;
+        for (int i = 0; i <= j; ++i) {
+            al[i] = (float)(alpha_d[i] * ig);
+            float bb = (float)(beta_d[i] * ig);
+            b2[i] = bb * bb;
+        }
+        ext = tri_extreme(al, b2, j + 1, G);
+        if (j + 1 >= LANCZOS_KMIN && fabs(fabs(ext) - prev) <= LANCZOS_RTOL * fabs(ext)) break;
+        if (bn.hi <= 1e-30 * fabs(a.hi) || j + 1 == LANCZOS_KMAX) break;
+        prev = fabs(ext);
+        beta = bn;
+        const dd ib = dd_of(1.0) / bn;
+        const int qn = ly.QB + (j + 1) * m;
+        for (int i = 0; i < m; ++i) S.set(qn + i, S.get(ly.V0 + i) * ib);
+        qbord[j + 1] = wb * ib;
+    }
+    double y[LANCZOS_KMAX];
+    tri_eigvec(alpha_d, beta_d, k, ext, y);
+    double vbr = 0.0, nv = 0.0;
+    for (int j = 0; j < k; ++j) vbr = fma(y[j], qbord[j].hi, vbr);
+    for (int i = 0; i < m; ++i) {
+        double v = 0.0;
+        for (int j = 0; j < k; ++j) v = fma(y[j], S.hi(ly.QB + j * m + i), v);
+        S.set(ly.RV + i, dd_of(v));
+        nv = fma(v, v, nv);
+    }
+    nv = fma(vbr, vbr, nv);
+    const double inv = nv > 0.0 ? rsqrt(nv) : 0.0;
+    for (int i = 0; i < m; ++i) S.set(ly.RV + i, dd_of(S.hi(ly.RV + i) * inv));
+    *vb = vbr * inv;
+    return ext;
+}
+
+// lambda_max of A by Lanczos on A (well conditioned: float64 products with
+// the hi parts of Phi), from the near-constant start of the float64 search
+__device__ double lanczos_max_dd(const LaneDD& S, const LayoutDD& ly, int n) {
+    const int m = ly.m;
+    float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
+    double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX];
+    // float64 vectors in the lo slots of V1 (q), V2 (q_prev) and GV (w)
+    auto Q = [&](int r, int i) -> double& { return S.p[(int64_t)(2 * (r + i) + 1) * 32]; };
+    const int q_ = ly.V1, qp = ly.V2, w = ly.GV;
+    double nrm2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double v = i < n ? 1.0 + 0.01 * (cos(1.7 * i + 0.3) + 0.1) : 0.0;
+        Q(q_, i) = v;
+        Q(qp, i) = 0.0;
+        nrm2 += v * v;
+    }
+    double qb = 0.1, qpb = 0.0;
+    nrm2 += qb * qb;
+    double inrm = rsqrt(nrm2);
+    for (int i = 0; i < n; ++i) Q(q_, i) *= inrm;
+    qb *= inrm;
+    double beta = 0.0, prev = -1.0, ext = 0.0;
+    for (int j = 0; j < LANCZOS_KMAX; ++j) {
+        // w = Phi q + qb 1 (rows < n), border 1^T q
+        double sumq = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < m; ++k) acc = fma(S.hi(ly.PH + (i >= k ? pk(i, k) : pk(k, i))), Q(q_, k), acc);
+            Q(w, i) = i < n ? acc + qb : acc;
+            if (i < n) sumq += Q(q_, i);
+        }
+        double wb = sumq;
+        double a = 0.0;
+        for (int i = 0; i < m; ++i) {
+            Q(w, i) = fma(-beta, Q(qp, i), Q(w, i));
+            a = fma(Q(q_, i), Q(w, i), a);
+        }
+        wb = fma(-beta, qpb, wb);
+        a = fma(qb, wb, a);
+        double bn = 0.0;
+        for (int i = 0; i < m; ++i) {
+            Q(w, i) = fma(-a, Q(q_, i), Q(w, i));
+            bn = fma(Q(w, i), Q(w, i), bn);
+        }
+        wb = fma(-a, qb, wb);
+        bn = sqrt(fma(wb, wb, bn));
+        alpha_d[j] = a;
+        beta_d[j] = bn;
+        double G = 0.0;
+        for (int i = 0; i <= j; ++i)
+            G = fmax(G, fabs(alpha_d[i]) + (i < j ? beta_d[i] : 0.0) + (i > 0 ? beta_d[i - 1] : 0.0));
+        const double ig = 1.0 / G;
+        for (int i = 0; i <= j; ++i) {
+            al[i] = (float)(alpha_d[i] * ig);
+            float bb = (float)(beta_d[i] * ig);
+            b2[i] = bb * bb;
+        }
+        ext = tri_max_abs(al, b2, j + 1, G);
+        if (j + 1 >= 2 && fabs(ext - prev) <= LANCZOS_RTOL * ext) break;
+        if (bn <= 1e-14 * fabs(a)) break;
+        prev = ext;
+        beta = bn;
+        const double ib = 1.0 / bn;
+        for (int i = 0; i < m; ++i) {
+            Q(qp, i) = Q(q_, i);
+            Q(q_, i) = Q(w, i) * ib;
+        }
+        qpb = qb;
+        qb = wb * ib;
+    }
+    return ext;
+}
+
+// d(-ln lambda_min)/dx by Hellmann-Feynman (float64, hi parts), as the
+// float64 search computes it
+__device__ double kappa_slope_dd(const LaneDD& S, const LayoutDD& ly, int n, int kernel, double eps_s,
+                                 double theta) {
+    double acc = 0.0;
+    for (int i = 1; i < n; ++i) {
+        double row = 0.0;
+        for (int j = 0; j < i; ++j) {
+            double ph = S.hi(ly.PH + pk(i, j));
+            double g = kernel == RBFFD_GAUSSIAN ? 2.0 * ph : ph * ph * ph;
+            row = fma(g * S.hi(ly.R2 + pk(i, j)), S.hi(ly.RV + j), row);
+        }
+        acc = fma(S.hi(ly.RV + i), row, acc);
+    }
+    return -eps_s * theta * (-2.0 * eps_s * acc);
+}
+
+// kappa_2(A(eps_s)) in double-double; theta (the A^{-1} Ritz value) and the
+// Schur complement s = 1^T Phi^{-1} 1 for the weights
+__device__ double eval_kappa_dd(const LaneDD& S, const LayoutDD& ly, int n, int kernel, double eps_s,
+                                double* theta_out, dd* schur, uint64_t seed) {
+    *theta_out = NAN;
+    *schur = dd_of(0.0);
+    assemble_dd(S, ly, n, kernel, eps_s);
+    if (!cholesky_dd(S, ly)) return INFINITY;
+    for (int i = 0; i < ly.m; ++i) S.set(ly.U + i, dd_of(i < n ? 1.0 : 0.0));
+    chol_solve_dd(S, ly, ly.U);
+    dd s = dd_of(0.0);
+    for (int i = 0; i < n; ++i) s = s + S.get(ly.U + i);
+    if (!(s.hi > 0.0)) return INFINITY;
+    *schur = s;
+    double vb;
+    double theta = lanczos_inv_dd(S, ly, n, s, seed, &vb);
+    double lmax = lanczos_max_dd(S, ly, n);
+    double k = lmax * fabs(theta);
+    if (!isfinite(k)) return INFINITY;
+    *theta_out = theta;
+    return k;
+}
+
+// first row of L_P from the factorised Phi(eps_s) (the reassociated
+// four-solve form of the float64 path), into V0 (first n entries)
+__device__ void weights_dd(const LaneDD& S, const LayoutDD& ly, int n, int kernel, double eps_s, dd s) {
+    const int m = ly.m, XS = ly.XS;
+    const dd e2 = two_prod(eps_s, eps_s);
+    const dd n0x = S.get(ly.NS), n0y = S.get(ly.NS + m), n0z = S.get(ly.NS + 2 * m);
+    // rhs_d,j = psi(r_0j) [P_0 (x_0 - x_j)]_d in V0, V1, V2
+    const int G[3] = {ly.V0, ly.V1, ly.V2};
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < m; ++i) S.set(G[d] + i, dd_of(0.0));
+    for (int j = 1; j < n; ++j) {
+        dd ps = psi_from_phi_dd(kernel, e2, S.get(ly.PH + pk(j, 0)));
+        dd dx = -S.get(XS + j), dy = -S.get(XS + m + j), dz = -S.get(XS + 2 * m + j);
+        dd nd = n0x * dx + n0y * dy + n0z * dz;
+        S.set(G[0] + j, ps * fms(dx, n0x, nd));
+        S.set(G[1] + j, ps * fms(dy, n0y, nd));
+        S.set(G[2] + j, ps * fms(dz, n0z, nd));
+    }
+    for (int d = 0; d < 3; ++d) aug_solve_dd(S, ly, n, G[d], dd_of(0.0), s);
+    // h_i = P_i g_i
+    for (int i = 0; i < n; ++i) {
+        dd gx = S.get(G[0] + i), gy = S.get(G[1] + i), gz = S.get(G[2] + i);
+        dd nx = S.get(ly.NS + i), ny = S.get(ly.NS + m + i), nz = S.get(ly.NS + 2 * m + i);
+        dd nd = nx * gx + ny * gy + nz * gz;
+        S.set(ly.HV + i, fms(gx, nx, nd));
+        S.set(ly.HV + m + i, fms(gy, ny, nd));
+        S.set(ly.HV + 2 * m + i, fms(gz, nz, nd));
+    }
+    // v_j = sum_i psi_ij (x_i - x_j) . h_i
+    for (int i = 0; i < m; ++i) S.set(ly.GV + i, dd_of(0.0));
+    for (int i = 0; i < n; ++i) {
+        const dd xi = S.get(XS + i), yi = S.get(XS + m + i), zi = S.get(XS + 2 * m + i);
+        const dd hx = S.get(ly.HV + i), hy = S.get(ly.HV + m + i), hz = S.get(ly.HV + 2 * m + i);
+        dd vi = S.get(ly.GV + i);
+        for (int j = 0; j < i; ++j) {
+            dd ps = psi_from_phi_dd(kernel, e2, S.get(ly.PH + pk(i, j)));
+            dd dx = xi - S.get(XS + j), dy = yi - S.get(XS + m + j), dz = zi - S.get(XS + 2 * m + j);
+            dd hjx = S.get(ly.HV + j), hjy = S.get(ly.HV + m + j), hjz = S.get(ly.HV + 2 * m + j);
+            S.set(ly.GV + j, S.get(ly.GV + j) + ps * (dx * hx + dy * hy + dz * hz));
+            vi = vi - ps * (dx * hjx + dy * hjy + dz * hjz);
+        }
+        S.set(ly.GV + i, vi);
+    }
+    for (int i = 0; i < m; ++i) S.set(ly.V0 + i, S.get(ly.GV + i));
+    aug_solve_dd(S, ly, n, ly.V0, dd_of(0.0), s);
+}
+
+struct SearchDDArgs {
+    SearchArgs a;                // inputs, outputs and search options as for the float64 kernel
+    const double* eps_fixed;     // node order: weights at these eps (no search), or NULL
+};
+
+__global__ void __launch_bounds__(64) search_dd_kernel(SearchDDArgs D) {
+    const SearchArgs& A = D.a;
+    const int lane_id = threadIdx.x & 31;
+    const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    LaneDD S{A.scratch + warp_global * 32 * (int64_t)A.lane_size * 2 + lane_id};
+    for (int g = 0; g < A.gi.ngroups; ++g) {
+        const LayoutDD ly = make_layout_dd(A.gi.npad[g]);
+        const int n = A.gi.n[g], npad = A.gi.npad[g];
+        const int64_t off = A.gi.ell_off[g];
+        const int64_t cnt = A.gi.row_begin[g + 1] - A.gi.row_begin[g];
+        while (true) {
+            const int64_t lr = (int64_t)atomicAdd(&A.counters[g], 1ull);
+            if (lr >= cnt) break;
+            const int64_t r = A.gi.row_begin[g] + lr;
+            const int node = A.row_node[r];
+            Geo geo = geometry_dd(S, ly, n, A.idx, off, npad, lr, A.X, A.NR);
+            Search st;
+            st.phase = PH_FIRST;
+            st.evals = 0;
+            st.status = RBFFD_STENCIL_OK;
+            st.lo = -INFINITY;
+            st.hi = INFINITY;
+            st.dx_prev = INFINITY;
+            st.f_prev = INFINITY;
+            st.ulo = A.xlo;
+            st.uhi = A.xhi;
+            dd schur = dd_of(0.0);
+            bool valid;
+            double eps_w;   // the eps_s whose factorisation is in scratch
+            if (D.eps_fixed) {
+                // weights at the given eps: factorise, no kappa
+                const double eps_s = D.eps_fixed[node] * geo.rs;
+                eps_w = eps_s;
+                assemble_dd(S, ly, n, A.kernel, eps_s);
+                valid = isfinite(eps_s) && eps_s > 0.0 && cholesky_dd(S, ly);
+                if (valid) {
+                    for (int i = 0; i < ly.m; ++i) S.set(ly.U + i, dd_of(i < n ? 1.0 : 0.0));
+                    chol_solve_dd(S, ly, ly.U);
+                    for (int i = 0; i < n; ++i) schur = schur + S.get(ly.U + i);
+                    valid = schur.hi > 0.0;
+                }
+                st.x_ret = log(eps_s);
+                st.k_ret = NAN;
+                st.status = RBFFD_STENCIL_OK;
+            } else {
+                const double tol_s = A.tol * geo.rs;
+                const float gs = A.guess_rows ? A.guess_rows[r] : NAN;
+                const bool learned = isfinite(gs);
+                st.x_next = clampd(learned ? (double)gs : log(1.0 / geo.mean_d), A.xlo, A.xhi);
+                const double acc_lo = A.acc_lo * A.kT * (1.0 + ACCEPT_MARGIN);
+                const double acc_hi = A.acc_hi * A.kT * (1.0 - ACCEPT_MARGIN);
+                while (st.phase != PH_DONE) {
+                    const double eps_s = exp(st.x_next);
+                    double theta;
+                    const double k = eval_kappa_dd(S, ly, n, A.kernel, eps_s, &theta, &schur, (uint64_t)node);
+                    const bool accept_now = learned && st.phase == PH_FIRST && k >= acc_lo && k <= acc_hi;
+                    const double dF = (isfinite(k) && !accept_now) ? kappa_slope_dd(S, ly, n, A.kernel, eps_s, theta)
+                                                                   : NAN;
+                    search_update(st, F_of(k, A.kT), dF, k, tol_s, A.max_evals, acc_lo, acc_hi, learned, n);
+                }
+                // the search stops at its last evaluated point, still factorised
+                valid = isfinite(st.k_ret) && schur.hi > 0.0;
+                eps_w = exp(st.x_ret);
+            }
+            if (valid) weights_dd(S, ly, n, A.kernel, eps_w, schur);
+            const double inv_rs2 = 1.0 / (geo.rs * geo.rs);
+            for (int j = 0; j < npad; ++j) {
+                const double w = (valid && j < n) ? (S.get(ly.V0 + j) * inv_rs2).hi : 0.0;
+                A.w64[ell_elem(off, npad, lr, j)] = w;
+                A.w32[ell_elem(off, npad, lr, j)] = (float)w;
+            }
+            if (!D.eps_fixed) {
+                A.eps[node] = exp(st.x_ret) / geo.rs;
+                A.kappa[node] = st.k_ret;
+                A.evals[node] = st.evals;
+            }
+            A.status[node] = valid ? st.status : RBFFD_STENCIL_SINGULAR;
+        }
+    }
+}
+
+}  // namespace
+
+rbffd_status build_search_dd(rbffd_op* op, const double* nodes, const double* normals,
+                             const rbffd_build_opts& o, const float* guess_rows, const double* eps_fixed,
+                             cudaStream_t st) {
+    const GroupInfo& gi = op->gi;
+    int mmax = 0;
+    for (int g = 0; g < gi.ngroups; ++g) mmax = std::max(mmax, gi.npad[g]);
+    const LayoutDD ly = make_layout_dd(mmax);
+    // one 64-thread block per SM: double-double scratch is large (~46 KB
+    // per lane at n = 31, ~0.5 MB at n = 128)
+    const int threads = 64;
+    const int64_t need = (op->N + threads - 1) / threads;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(), need));
+    const int64_t lanes = (int64_t)blocks * threads;
+    double* scratch = nullptr;
+    unsigned long long* ctr = nullptr;
+    RBFFD_CUDA_TRY(cudaMallocAsync(&scratch, (size_t)lanes * ly.size * 2 * sizeof(double), st));
+    RBFFD_CUDA_TRY(cudaMallocAsync(&ctr, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
+    RBFFD_CUDA_TRY(cudaMemsetAsync(ctr, 0, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
+    SearchDDArgs D;
+    SearchArgs& A = D.a;
+    A.X = nodes;
+    A.NR = normals;
+    A.w64 = op->w64;
+    A.w32 = op->w32;
+    A.idx = op->idx;
+    A.row_node = op->row_node;
+    A.gi = gi;
+    A.scratch = scratch;
+    A.lane_size = ly.size;
+    A.kernel = o.kernel;
+    A.kT = o.kappa_target;
+    A.tol = o.eps_tol;
+    A.xlo = o.eps_lo > 0.0 ? log(o.eps_lo) : -INFINITY;
+    A.xhi = o.eps_hi > 0.0 ? log(o.eps_hi) : INFINITY;
+    A.acc_lo = o.accept_lo;
+    A.acc_hi = o.accept_hi;
+    A.max_evals = o.max_evals;
+    A.guess_rows = guess_rows;
+    A.counters = ctr;
+    A.eps = op->eps;
+    A.kappa = op->kappa;
+    A.evals = op->evals;
+    A.status = op->status;
+    D.eps_fixed = eps_fixed;
+    search_dd_kernel<<<blocks, threads, 0, st>>>(D);
+    note_launch();
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    RBFFD_CUDA_TRY(cudaFreeAsync(scratch, st));
+    RBFFD_CUDA_TRY(cudaFreeAsync(ctr, st));
+    return RBFFD_OK;
+}
+
+}  // namespace rbffd

@@ -122,6 +122,11 @@ rbffd_status build_search(rbffd_op* op, const double* nodes, const double* norma
                           const rbffd_build_opts& o, const float* eps_guess_s, cudaStream_t st);
 rbffd_status build_weights(rbffd_op* op, const double* nodes, const double* normals,
                            const rbffd_build_opts& o, const double* eps_node, cudaStream_t st);
+// the same in double-double arithmetic: the search (eps_fixed == NULL) or the
+// weights at the given node-order eps; per-stencil statuses as build_search
+rbffd_status build_search_dd(rbffd_op* op, const double* nodes, const double* normals,
+                             const rbffd_build_opts& o, const float* guess_rows, const double* eps_fixed,
+                             cudaStream_t st);
 // mlp.cu: predicted ln(eps * r_s) for every internal row of groups with a network
 rbffd_status mlp_guess(const rbffd_op* op, const double* nodes, const double* normals,
                        const rbffd_build_opts& o, float* guess_rows, cudaStream_t st);
