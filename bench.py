@@ -246,7 +246,7 @@ def configs_report(R, W, T, torch, nets):
     for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2), ("bumpy500k_learned", _c4),
                      ("bumpy2m_pointcloud", _c5), ("sphere_heat_convergence_bdf4", _e3),
                      ("forced_sphere_convergence_bdf4", _e4), ("forced_torus_convergence_bdf4", _e5),
-                     ("forced_fixed_kappa_1e14", _e6)):
+                     ("forced_fixed_kappa_1e14", _e6), ("forced_fixed_kappa_1e20_dd", _e6_dd)):
         try:
             out[name] = fn(R, W, T, torch, nets)
         except Exception as e:   # reported, not hidden
@@ -385,6 +385,12 @@ def _e5(R, W, T, torch, nets):
 def _e6(R, W, T, torch, nets):
     return {"forced_sphere": convergence_study(R, W, T, torch, "forced_sphere", kappa=1e14),
             "forced_torus": convergence_study(R, W, T, torch, "forced_torus", kappa=1e14)}
+
+
+def _e6_dd(R, W, T, torch, nets):
+    # kappa_T = 1e20: double-double builds (Section 6 uses quad precision)
+    return {"forced_sphere": convergence_study(R, W, T, torch, "forced_sphere", kappa=1e20),
+            "forced_torus": convergence_study(R, W, T, torch, "forced_torus", kappa=1e20)}
 
 
 def _ev(torch):

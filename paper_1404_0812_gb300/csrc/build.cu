@@ -831,6 +831,13 @@ __device__ void search_update(Search& s, double f, double d, double k, double to
         finish(s, x, k, RBFFD_STENCIL_OK);
         return;
     }
+    // without a usable slope: the same test with the flattest slope that
+    // would have been trusted (0.2 |model|); it stops an iteration sitting
+    // on the root (|F| at rounding level) whose Ritz vector gives no slope
+    if (!usable && f != F_FAIL && fabs(f) < 0.1 * xtol * fabs(sm)) {
+        finish(s, x, k, RBFFD_STENCIL_OK);
+        return;
+    }
     if (bracketed && s.hi - s.lo < xtol) {
         finish(s, x, k, RBFFD_STENCIL_OK);
         return;
