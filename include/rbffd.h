@@ -336,7 +336,7 @@ rbffd_status rbffd_stencil_weights_noalloc(const double* nodes, const double* no
 
 /* ------------------------------------------------------------------------
  * Learned shape-parameter warm start (not in the paper; the paper's search
- * of Section 5 stays as the fallback and the judge).
+ * of Section 5 stays as the fallback and the arbiter).
  * Features of a stencil (3n floats): tangent-frame offsets (t1.d, t2.d,
  * nh.d) / r_s of every stencil node (centre first), with nh oriented so
  * sum nh.d <= 0, t1 the unit tangent part of the nearest neighbour's offset,

@@ -2,7 +2,7 @@
 
 The paper searches eps per stencil (Section 5).  The learned part predicts
 that eps from the stencil's tangent-plane geometry and hands it to the
-search as a first guess; the search stays the judge.  Definitions, in
+search as a first guess; the search stays the arbiter.  Definitions, in
 float64:
 
 Features of a stencil P = (x_1 .. x_n) with unit normal nh at the centre

@@ -1,5 +1,5 @@
 // Learned shape-parameter warm start (not in the paper; it feeds the
-// Section 5 search a first guess, and the search stays the judge).
+// Section 5 search a first guess, and the search stays the arbiter).
 //
 // Features (float64 geometry, stored float32): tangent-frame offsets
 // (t1.d, t2.d, nh.d) / r_s of every stencil node, with nh oriented so that

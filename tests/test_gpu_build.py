@@ -1,7 +1,7 @@
 """GPU parity of the operator build (stencils, shape parameters, weights) and
 of the apply, through the C ABI, against the CPU oracle.
 
-Tolerances (floating point; derived in the design doc from the arithmetic):
+Tolerances (floating point; derived from the arithmetic):
 * applied operator, smooth u: ||L_gpu u - L_cpu u||_inf / ||L_cpu u||_inf
   <= 1e-8 (also at kappa_T = 1e12);
 * applied operator, random u at kappa_T = 1e12: <= 5e-5 -- two exact-in-
