@@ -244,7 +244,8 @@ def configs_report(R, W, T, torch, nets):
     its error instead of its numbers."""
     out = {}
     for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2), ("bumpy500k_learned", _c4),
-                     ("bumpy2m_pointcloud", _c5), ("sphere_heat_convergence_bdf4", _e3),
+                     ("bumpy2m_pointcloud", _c5), ("reorder_1m_shuffled", _reorder),
+                     ("sphere_heat_convergence_bdf4", _e3),
                      ("forced_sphere_convergence_bdf4", _e4), ("forced_torus_convergence_bdf4", _e5),
                      ("forced_fixed_kappa_1e14", _e6), ("forced_fixed_kappa_1e20_dd", _e6_dd)):
         try:
@@ -368,6 +369,59 @@ def convergence_study(R, W, T, torch, problem="heat_sphere", stencil_sizes=(11, 
 def sphere_heat_study(R, W, T, torch, stencil_sizes=(11, 17, 31), levels=(3, 4, 5, 6), kappa="grow", **kw):
     """The heat-equation study of Section 6 (see convergence_study)."""
     return convergence_study(R, W, T, torch, "heat_sphere", stencil_sizes, levels, kappa, **kw)
+
+
+def _reorder(R, W, T, torch, nets):
+    """Section 4.1's reordering on a node set without any order: the 1M-node
+    Fibonacci sphere shuffled (seed 9), n = 50, learned build; apply (float32)
+    and SBDF2 steps (Schnakenberg float32, CUDA graph) as given, after a Morton
+    renumbering and after reverse Cuthill-McKee."""
+    import numpy as np
+    ns = W.fibonacci_sphere(N_NODES)
+    p = np.random.default_rng(9).permutation(ns.N)
+    X0, N0 = ns.X[p].copy(), ns.normals[p].copy()
+    net = [nets[SIZES.index(50)]] if nets is not None else None
+    s = W.SCHNAKENBERG
+    name, coef = R.model_coefs(s)
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    out = {}
+
+    def measure(X, Nr, u, v):
+        op = R.build_operator(T(X), T(Nr), 50, kernel="imq", kappa_target=KAPPA_T, mlps=net)
+        uu = T(u, torch.float32)
+        yy = torch.empty_like(uu)
+        for _ in range(3):
+            R.apply(op, uu, yy)
+        a, b = _ev(torch)
+        a.record()
+        for _ in range(20):
+            R.apply(op, uu, yy)
+        b.record()
+        torch.cuda.synchronize()
+        ams = a.elapsed_time(b) / 20
+        sp = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
+                          delta_v=s["delta_v"], coef=coef, tol=1e-6, use_graph=True)
+        st = R.StepState.create(T(u, torch.float32), T(v, torch.float32))
+        R.step_imex(op, st, sp, 2)
+        a.record()
+        R.step_imex(op, st, sp, 20)
+        b.record()
+        torch.cuda.synchronize()
+        return op, {"apply_f32_GB_s": round(op.apply_bytes(R.F32) / (ams * 1e-3) / 1e9, 1),
+                    "step_ms": round(a.elapsed_time(b) / 20, 3)}
+
+    op, out["shuffled"] = measure(X0, N0, u0, v0)
+    t0 = time.time()
+    pm = R.morton_order(T(X0)).cpu().numpy()
+    tm = time.time() - t0
+    t0 = time.time()
+    pr = R.rcm_order(op).cpu().numpy()
+    tr = time.time() - t0
+    del op
+    for label, perm, secs in (("morton", pm, tm), ("rcm", pr, tr)):
+        _, out[label] = measure(X0[perm], N0[perm], u0[perm], v0[perm])
+        out[label]["ordering_s"] = round(secs, 2)
+    return out
 
 
 def _e3(R, W, T, torch, nets):

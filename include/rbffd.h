@@ -335,6 +335,30 @@ rbffd_status rbffd_stencil_weights_noalloc(const double* nodes, const double* no
                                            void* stream);
 
 /* ------------------------------------------------------------------------
+ * Locality orderings of the nodes (Section 4.1 reorders L_X by reverse
+ * Cuthill-McKee for faster iterative solves).  Each returns perm (N int32,
+ * perm[k] = the original index of the node placed k-th); the library never
+ * reorders on its own: the caller applies perm to its node, normal and field
+ * arrays (x_new[k] = x[perm[k]]) and builds on the reordered set.  The sorts
+ * and searches run on the host (one-off O(N log N) / O(nnz) steps);
+ * synchronous.
+ * ---------------------------------------------------------------------- */
+
+/* Z-order (Morton) of the nodes: 21-bit quantisation of each coordinate
+ * over the bounding cube, bits interleaved x-y-z, ties by index.
+ * nodes: device N x 3 float64; perm: device out. */
+rbffd_status rbffd_morton_order(const double* nodes, int64_t N, int32_t* perm, void* stream);
+/* Reverse Cuthill-McKee (George-Liu) of op's stencil graph (node k linked
+ * to its n_k - 1 neighbours, symmetrised): per connected component a
+ * pseudo-peripheral start, breadth-first visits with neighbours in
+ * increasing degree (ties by index), the whole order reversed.  perm: device
+ * out, in op's node numbering. */
+rbffd_status rbffd_rcm_order(const rbffd_op* op, int32_t* perm, void* stream);
+/* The same on a host CSR graph (rowptr N+1 int64, cols int32, symmetrised
+ * inside; self loops and repeats ignored); perm: host out.  Needs no GPU. */
+rbffd_status rbffd_rcm_order_host(const int64_t* rowptr, const int32_t* cols, int64_t N, int32_t* perm);
+
+/* ------------------------------------------------------------------------
  * Learned shape-parameter warm start (not in the paper; the paper's search
  * of Section 5 stays as the fallback and the arbiter).
  * Features of a stencil (3n floats): tangent-frame offsets (t1.d, t2.d,

@@ -213,6 +213,38 @@ def get_ell(op: Operator):
     return out
 
 
+def morton_order(nodes, stream=None):
+    """rbffd_morton_order -> CUDA int32 perm (perm[k] = original index of the
+    k-th node in Z-order)."""
+    nodes = _dev(nodes, torch.float64)
+    perm = torch.empty(nodes.shape[0], dtype=torch.int32, device="cuda")
+    _lib.check(_lib.load().rbffd_morton_order(_ptr(nodes), nodes.shape[0], _ptr(perm), _stream(stream)),
+               "rbffd_morton_order")
+    return perm
+
+
+def rcm_order(op: Operator, stream=None):
+    """rbffd_rcm_order -> CUDA int32 perm of op's stencil graph (Section 4.1's
+    reverse Cuthill-McKee)."""
+    perm = torch.empty(op.N, dtype=torch.int32, device="cuda")
+    _lib.check(_lib.load().rbffd_rcm_order(op.handle, _ptr(perm), _stream(stream)), "rbffd_rcm_order")
+    return perm
+
+
+def rcm_order_host(rowptr, cols):
+    """rbffd_rcm_order_host on a host CSR graph (numpy) -> numpy int32 perm."""
+    import numpy as np
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    N = rowptr.shape[0] - 1
+    perm = np.empty(N, dtype=np.int32)
+    _lib.check(_lib.load(build=False).rbffd_rcm_order_host(rowptr.ctypes.data_as(C.c_void_p),
+                                                           cols.ctypes.data_as(C.c_void_p), N,
+                                                           perm.ctypes.data_as(C.c_void_p)),
+               "rbffd_rcm_order_host")
+    return perm
+
+
 def get_rows(op: Operator, stream=None):
     """rbffd_get_rows -> (idx int32 N x n_max, w float64 N x n_max)."""
     lib = _lib.load()

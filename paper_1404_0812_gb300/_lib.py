@@ -95,6 +95,9 @@ SIGNATURES = {
     "rbffd_selftest_barrier_timeout": (C.c_int, [vp]),
     "rbffd_stencil_weights_noalloc": (C.c_int, [vp, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int,
                                                 vp, vp]),
+    "rbffd_morton_order": (C.c_int, [vp, C.c_int64, vp, vp]),
+    "rbffd_rcm_order": (C.c_int, [vp, vp, vp]),
+    "rbffd_rcm_order_host": (C.c_int, [vp, vp, C.c_int64, vp]),
     "rbffd_status_str": (C.c_char_p, [C.c_int]),
     "rbffd_last_error": (C.c_char_p, []),
     "rbffd_fp64_peak": (C.c_int, [vp, C.POINTER(C.c_double)]),
