@@ -30,9 +30,13 @@ def R():
 
 
 @pytest.fixture(scope="module")
-def built(R):
+def nets(R):
     import bench
-    nets = bench.train_networks(R, W, T, torch)
+    return bench.train_networks(R, W, T, torch)
+
+
+@pytest.fixture(scope="module")
+def built(R, nets):
     ns = W.fibonacci_sphere(1_000_000)
     nper = W.stencil_size_groups(ns.N, SIZES)
     op = R.build_operator(T(ns.X), T(ns.normals), T(nper, torch.int32), kernel="imq", kappa_target=1e12,
@@ -96,3 +100,53 @@ def test_full_size_step_satisfies_its_equations(R, built, dtype, tol, bound):
         rhs = x0 + s["dt"] * r0
         res = np.linalg.norm(x - s["dt"] * d * Lx - rhs) / np.linalg.norm(rhs)
         assert res < bound, res
+
+
+def test_pointcloud_2m_build_sampled_rows(R, nets):
+    """The 2M-node bumpy point cloud (Gaussian tangent jitter 0.25 h, 20-NN
+    PCA normals), n = 70, kappa_T = 1e12, learned start as the bench builds
+    it: sampled rows against the oracle."""
+    ns = W.workload("bumpy2m")
+    n = 70
+    op = R.build_operator(T(ns.X), T(ns.normals), n, kernel="imq", kappa_target=1e12,
+                          mlps=[nets[SIZES.index(n)]], allow_failures=True)
+    info = {k: v.cpu().numpy() for k, v in R.get_stencil_info(op).items()}
+    assert np.all((info["status"] == 0) | (info["status"] == 4))
+    acc = info["status"] == 4
+    assert np.all((info["kappa"][acc] >= 0.5e12) & (info["kappa"][acc] <= 2e12))
+    idx, w = R.get_rows(op)
+    rows = np.random.default_rng(2).choice(ns.N, 8, replace=False)
+    sel = torch.as_tensor(rows, device="cuda")
+    idx_r, w_r = idx[sel].cpu().numpy(), w[sel].cpu().numpy()
+    for r, k in enumerate(rows):
+        sref = ost.stencil(ns.X, int(k), n)
+        assert np.array_equal(idx_r[r, :n], sref.astype(np.int32))
+        P = ns.X[sref]
+        kc = ow.cond2(ow.interp_matrix(P, info["eps"][k], ow.IMQ))
+        assert abs(np.log(kc / info["kappa"][k])) < 1e-3
+        wref = ow.stencil_weights(P, ns.normals[sref], info["eps"][k], ow.IMQ)
+        assert np.abs(w_r[r, :n] - wref).max() <= 5e-4 * np.abs(wref).max()
+
+
+def test_torus_40k_schnakenberg_float32_against_float64_oracle(R):
+    """The staggered torus m = 82 (N = 40,344), n = 50, kappa_T = 1e12:
+    100 float32 Schnakenberg steps on the GPU against the oracle's float64
+    stepper driven by the same operator's weights (<= 1e-5)."""
+    import scipy.sparse as sps
+    from oracle import stepping as ostp
+    ns = W.workload("torus40344")
+    n = 50
+    op = R.build_operator(T(ns.X), T(ns.normals), n, kernel="imq", kappa_target=1e12)
+    idx, w = (t.cpu().numpy() for t in R.get_rows(op))
+    Lx = sps.csr_matrix((w[:, :n].ravel(), idx[:, :n].ravel(), np.arange(0, ns.N * n + 1, n)), shape=(ns.N, ns.N))
+    s = W.SCHNAKENBERG
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    o = ostp.imex_run(lambda x: Lx @ x, u0, v0, s, 100)
+    name, coef = R.model_coefs(s)
+    p = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
+                     delta_v=s["delta_v"], coef=coef, tol=1e-8, use_graph=True)
+    st = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
+    R.step_imex(op, st, p, 100)
+    for x, ref in ((st.u, o["u"]), (st.v, o["v"])):
+        got = x.cpu().numpy().astype(np.float64)
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
