@@ -196,7 +196,9 @@ __device__ __forceinline__ void load4(const double* p, double (&w)[4]) {
     w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
 }
 
-// (L x0)_row and (L x1)_row in one pass over the row (x read L1-bypassing)
+// (L x0)_row and (L x1)_row in one pass over the row (x read L1-bypassing:
+// within one launch L1 is not coherent across SMs); software-pipelined so
+// that a chunk's index and weight loads overlap the previous chunk's gathers
 template <typename T>
 __device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, const T* x0, const T* x1, bool two,
                                        T& y0, T& y1) {
@@ -204,24 +206,42 @@ __device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, const T* x0,
     const int npad = a.gi.npad[g];
     const int64_t base = ell_elem(a.gi.ell_off[g], npad, r - a.gi.row_begin[g], 0);
     T s0 = T(0), s1 = T(0);
+    int4 iv = __ldg(reinterpret_cast<const int4*>(a.idx + base));
+    T wv[4];
+    load4(a.w + base, wv);
     for (int jb = 0; jb < npad; jb += 4) {
-        const int64_t e = base + (int64_t)(jb >> 2) * 128;
-        int4 iv = __ldg(reinterpret_cast<const int4*>(a.idx + e));
-        int ii[4] = {iv.x, iv.y, iv.z, iv.w};
-        T wv[4];
-        load4(a.w + e, wv);   // one (float) or two (double) 16-byte loads
+        // the next chunk's index and weight loads go out before this chunk's gathers
+        int4 ivn = iv;
+        T wn[4] = {wv[0], wv[1], wv[2], wv[3]};
+        if (jb + 4 < npad) {
+            const int64_t en = base + (int64_t)((jb + 4) >> 2) * 128;
+            ivn = __ldg(reinterpret_cast<const int4*>(a.idx + en));
+            load4(a.w + en, wn);
+        }
+        const int ii[4] = {iv.x, iv.y, iv.z, iv.w};
+        T g0[4], g1[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            s0 = fma(wv[q], ldcg(x0 + ii[q]), s0);
-            if (two) s1 = fma(wv[q], ldcg(x1 + ii[q]), s1);
+            g0[q] = ldcg(x0 + ii[q]);
+            g1[q] = two ? ldcg(x1 + ii[q]) : T(0);
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            s0 = fma(wv[q], g0[q], s0);
+            s1 = fma(wv[q], g1[q], s1);
+        }
+        iv = ivn;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wv[q] = wn[q];
     }
     y0 = s0;
-    y1 = s1;
+    y1 = two ? s1 : T(0);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) step_kernel(Args<T> a) {
+// NT threads per block: 1024 (one block per SM, <= 64 registers) for large
+// operators, 256 for small ones
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool two = a.ns == 2;
@@ -572,7 +592,8 @@ template <typename T>
 rbffd_status launch_step(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
     RBFFD_CUDA_TRY(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned long long), st));
     void* args[] = {&a};
-    RBFFD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)step_kernel<T>, dim3(ws->blocks),
+    const void* fn = ws->threads == 1024 ? (const void*)step_kernel<T, 1024> : (const void*)step_kernel<T, 256>;
+    RBFFD_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ws->blocks),
                                                dim3(ws->threads), args, 0, st));
     note_launch();
     return RBFFD_OK;
@@ -653,15 +674,24 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         op->step = ws;
         ws->elem = elem;
         ws->N = op->N;
-        ws->threads = 256;
+        // Large operators: one 1024-thread block per SM, so that only one
+        // block per SM meets at each grid barrier (1M-node operator: 2.67 ms
+        // per step against 3.08 ms with 2 x 512 and 3.22 ms with 2 x 256
+        // threads per SM; 4 x 256 is slower still, 3.94 ms -- the barrier's
+        // cost grows with its blocks) once there is a row per thread.  Smaller
+        // ones keep 256-thread blocks (about four rows per thread) so that they
+        // still spread over the SMs.
+        ws->threads = op->N >= (int64_t)1024 * sm_count() ? 1024 : 256;
         int dev = 0, per_sm = 0;
         RBFFD_CUDA_TRY(cudaGetDevice(&dev));
-        if (elem == 4)
-            RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<float>, 256, 0));
-        else
-            RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<double>, 256, 0));
+        const void* fn = elem == 4 ? (ws->threads == 1024 ? (const void*)step_kernel<float, 1024>
+                                                          : (const void*)step_kernel<float, 256>)
+                                   : (ws->threads == 1024 ? (const void*)step_kernel<double, 1024>
+                                                          : (const void*)step_kernel<double, 256>);
+        RBFFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, ws->threads, 0));
         int64_t maxb = (int64_t)std::max(1, per_sm) * sm_count();
-        int64_t want = (op->N + 4 * 256 - 1) / (4 * 256);   // at least ~4 rows per thread
+        const int64_t rows_per_block = ws->threads == 1024 ? 1024 : 4 * 256;
+        int64_t want = (op->N + rows_per_block - 1) / rows_per_block;
         ws->blocks = (int)std::max<int64_t>(1, std::min(maxb, std::max<int64_t>(want, 1)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->vec, 2 * 7 * op->N * elem));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->partial, (size_t)NPHASE * ws->blocks * NSLOT * sizeof(double)));
