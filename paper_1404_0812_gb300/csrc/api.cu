@@ -79,6 +79,23 @@ __global__ void rows_kernel(const int32_t* __restrict__ idx, const double* __res
     }
 }
 
+// number of stencils whose status is neither OK nor an accepted prediction
+// (synchronises the stream)
+cudaError_t failed_stencils(const rbffd_op* op, cudaStream_t st, int* count) {
+    int* bad = nullptr;
+    cudaError_t e = cudaMallocAsync(&bad, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        count_status<<<(unsigned)((op->N + 255) / 256), 256, 0, st>>>(op->status, op->N, bad);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(count, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (bad) cudaFreeAsync(bad, st);
+    return e;
+}
+
 void free_op(rbffd_op* op) {
     if (!op) return;
     cudaFree(op->row_node);
@@ -269,15 +286,8 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
         TRY_OP(cudaEventRecord(ev[4], st));   // no separate weights phase
         if (guess) cudaFreeAsync(guess, st);
         if (s != RBFFD_OK) return fail(s);
-        int* bad = nullptr;
-        TRY_OP(cudaMallocAsync(&bad, sizeof(int), st));
-        TRY_OP(cudaMemsetAsync(bad, 0, sizeof(int), st));
-        count_status<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->status, N, bad);
-        note_launch();
         int hb = 0;
-        TRY_OP(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TRY_OP(cudaStreamSynchronize(st));
-        cudaFreeAsync(bad, st);
+        TRY_OP(failed_stencils(op, st, &hb));
         if (hb) {
             set_error("eps search failed for %d stencils", hb);
             search_status = RBFFD_EPS_SEARCH_FAILED;
@@ -292,15 +302,8 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
         if (o.precision == RBFFD_PREC_DD) {
             s = build_search_dd(op, nodes, normals, o, nullptr, op->eps, st);
             if (s != RBFFD_OK) return fail(s);
-            int* bad = nullptr;
-            TRY_OP(cudaMallocAsync(&bad, sizeof(int), st));
-            TRY_OP(cudaMemsetAsync(bad, 0, sizeof(int), st));
-            count_status<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->status, N, bad);
-            note_launch();
             int hb = 0;
-            TRY_OP(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-            TRY_OP(cudaStreamSynchronize(st));
-            cudaFreeAsync(bad, st);
+            TRY_OP(failed_stencils(op, st, &hb));
             if (hb) {
                 set_error("%d stencils have a local matrix that is not numerically positive definite", hb);
                 s = RBFFD_ESINGULAR;
