@@ -234,7 +234,8 @@ rbffd_status rbffd_get_stencil_info(const rbffd_op* op, double* eps, double* kap
                                     int32_t* evals, int32_t* status, void* stream);
 
 /* eps, kappa and evals of rbffd_get_stencil_info (Section 5), without the
- * status array. */
+ * status array (device outputs, each may be NULL; asynchronous copies).
+ * Returns RBFFD_EINVAL when op is NULL, RBFFD_ECUDA when a copy fails. */
 rbffd_status rbffd_get_eps(const rbffd_op* op, double* eps, double* kappa, int32_t* evals,
                            void* stream);
 
@@ -249,7 +250,8 @@ rbffd_status rbffd_get_eps(const rbffd_op* op, double* eps, double* kappa, int32
  * float32 copy); entries j >= n[g] hold the row's own node and weight 0,
  * and the rows that pad a group's last slice of 32 hold index 0 and weight
  * 0 (every index is a valid node).  All pointers are device memory
- * owned by op; the call itself touches no device memory.
+ * owned by op; the call itself touches no device memory.  Returns
+ * RBFFD_EINVAL on a NULL argument.
  */
 typedef struct {
     int ngroups;
@@ -341,7 +343,8 @@ rbffd_status rbffd_stencil_weights_noalloc(const double* nodes, const double* no
  * reorders on its own: the caller applies perm to its node, normal and field
  * arrays (x_new[k] = x[perm[k]]) and builds on the reordered set.  The sorts
  * and searches run on the host (one-off O(N log N) / O(nnz) steps);
- * synchronous.
+ * synchronous.  Errors: RBFFD_EINVAL (NULL argument, N out of range,
+ * non-finite coordinates, a column index out of range), RBFFD_ECUDA.
  * ---------------------------------------------------------------------- */
 
 /* Z-order (Morton) of the nodes: 21-bit quantisation of each coordinate
@@ -377,7 +380,8 @@ int64_t rbffd_mlp_param_count(int n);
 rbffd_status rbffd_mlp_create(int n, const float* params_host, rbffd_mlp** out);
 rbffd_status rbffd_mlp_get_params(const rbffd_mlp* mlp, float* params_host);
 /* Replace a network's parameters with host float32 params (layout above;
- * param_count floats) and reset its Adam state.  Synchronous. */
+ * param_count floats) and reset its Adam state.  Synchronous.  Returns
+ * RBFFD_EINVAL on a NULL argument, RBFFD_ECUDA when the copy fails. */
 rbffd_status rbffd_mlp_load(rbffd_mlp* mlp, const float* params_host);
 void rbffd_mlp_destroy(rbffd_mlp* mlp);
 
