@@ -166,6 +166,27 @@ __device__ __forceinline__ bool key_less(long long ka, int ia, long long kb, int
     return ka < kb || (ka == kb && ia < ib);
 }
 
+// Shell sort of (key, index) pairs by key_less (gaps 23, 10, 4, 1): the
+// (unique) pairs end in the same order as incremental insertion would give.
+__device__ void sort_keys(long long* k, int* v, int n) {
+    const int gaps[4] = {23, 10, 4, 1};
+    for (int gi = 0; gi < 4; ++gi) {
+        const int gap = gaps[gi];
+        for (int i = gap; i < n; ++i) {
+            const long long tk = k[i];
+            const int tv = v[i];
+            int j = i;
+            while (j >= gap && key_less(tk, tv, k[j - gap], v[j - gap])) {
+                k[j] = k[j - gap];
+                v[j] = v[j - gap];
+                j -= gap;
+            }
+            k[j] = tk;
+            v[j] = tv;
+        }
+    }
+}
+
 // One thread per query, queries taken in cell-sorted order so that the 32
 // queries of a warp share nearby cells.
 __global__ void __launch_bounds__(128)
@@ -220,8 +241,22 @@ knn_query(const double* __restrict__ X, const int32_t* __restrict__ node_row, in
                         double d2 = sq_dist(qx, qy, qz, sx[3 * (int64_t)p], sx[3 * (int64_t)p + 1],
                                             sx[3 * (int64_t)p + 2]);
                         const long long kd = __double_as_longlong(d2);
-                        if (cnt == K && !key_less(kd, j, bk[K - 1], bi[K - 1])) continue;
-                        int i = cnt < K ? cnt++ : K - 1;
+                        if (cnt < K) {
+                            // the first K candidates arrive in no useful order:
+                            // gather them unsorted and sort once when the list fills
+                            bk[cnt] = kd;
+                            bi[cnt] = j;
+                            if (++cnt == K) {
+                                sort_keys(bk, bi, K);
+                                double kth = __longlong_as_double(bk[K - 1]);
+                                kth_f = (float)(kth * (1.0 + 1e-6) + 4.0 * g.delta * sqrt(kth) +
+                                                4.0 * g.delta * g.delta) * (1.0f + 1e-6f);
+                            }
+                            continue;
+                        }
+                        if (!key_less(kd, j, bk[K - 1], bi[K - 1])) continue;
+                        // later candidates come from outer shells and land near the end
+                        int i = K - 1;
                         while (i > 0 && key_less(kd, j, bk[i - 1], bi[i - 1])) {
                             bk[i] = bk[i - 1];
                             bi[i] = bi[i - 1];
