@@ -294,3 +294,18 @@ def test_degenerate_sizes_rejected(R):
     with pytest.raises(R.RbffdError) as e:
         R.build_operator(X, Nr, T(nper, torch.int32))
     assert e.value.status == 1
+
+
+def test_invalid_options_are_rejected(R):
+    ns = W.icosahedral_sphere(1)
+    X, Nr = T(ns.X), T(ns.normals)
+    for kw in (dict(kappa_target=1.0), dict(kappa_target=float("inf")), dict(eps_tol=0.0), dict(max_evals=1),
+               dict(kernel=7), dict(block_threads=48), dict(precision="quad")):
+        with pytest.raises((R.RbffdError, KeyError)) as e:
+            R.build_operator(X, Nr, 10, **kw)
+        if isinstance(e.value, R.RbffdError):
+            assert e.value.status == 1, kw
+    net = R.EpsNet(10)
+    with pytest.raises(R.RbffdError) as e:
+        R.build_operator(X, Nr, 10, mlps=[net], accept=(2.0, 0.5))
+    assert e.value.status == 1

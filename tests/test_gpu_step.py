@@ -299,3 +299,17 @@ def test_forced_sphere_bdf4_source_parity(R, sphere2562):
         R.step_imex(op, st, p, 25)        # the device time continues across calls
         assert st.t == pytest.approx(3 * dt + 40 * dt)
         assert rel_inf(st.u.cpu().numpy().astype(np.float64), o["u"]) <= bound
+
+
+def test_invalid_step_parameters_are_rejected(R):
+    ns = W.icosahedral_sphere(1)
+    op = R.build_operator(T(ns.X), T(ns.normals), 10, kernel="imq", eps_override=T(np.full(ns.N, 2.0)))
+    st = R.StepState.create(T(W.sph_harm_y32(ns.X)))
+    for kw in (dict(dt=0.0), dict(tol=0.0), dict(maxit=0), dict(nspecies=3), dict(model="barrio", nspecies=1)):
+        base = dict(model="none", nspecies=1, dtype=torch.float64, dt=1e-3)
+        base.update(kw)
+        with pytest.raises(R.RbffdError) as e:
+            R.step_imex(op, st, R.StepParams(**base), 1)
+        assert e.value.status == 1, kw
+    with pytest.raises(R.RbffdError):     # two species without the v state
+        R.step_imex(op, st, R.StepParams(model="none", nspecies=2, dtype=torch.float64, dt=1e-3), 1)
