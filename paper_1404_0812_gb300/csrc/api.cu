@@ -176,7 +176,15 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
         RBFFD_CUDA_TRY(cudaMemcpyAsync(hn.data(), n_per_node, N * sizeof(int32_t),
                                        cudaMemcpyDeviceToHost, st));
         RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int64_t i = 0; i < N; ++i) counts[hn[i]]++;
+        // flat histogram over the admissible sizes (a map per node is slow at N = 1M)
+        std::vector<int64_t> hist(RBFFD_MAX_N + 1, 0);
+        for (int64_t i = 0; i < N; ++i) {
+            const int32_t v = hn[i];
+            RBFFD_CHECK_ARG(v >= 2 && v <= RBFFD_MAX_N, "stencil size must be in [2, 128]");
+            hist[v]++;
+        }
+        for (int v = 2; v <= RBFFD_MAX_N; ++v)
+            if (hist[v]) counts[v] = hist[v];
     } else {
         counts[n_uniform] = N;
     }
@@ -234,13 +242,9 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     TRY_OP(cudaMemsetAsync(op->w32, 0, op->ell_elems * sizeof(float), st));
     if (n_per_node) {
         std::vector<int32_t> rn(N);
-        std::vector<int64_t> pos(gi.ngroups);
-        for (int g = 0; g < gi.ngroups; ++g) pos[g] = gi.row_begin[g];
-        for (int64_t i = 0; i < N; ++i) {
-            int g = 0;
-            while (gi.n[g] != hn[i]) ++g;
-            rn[pos[g]++] = (int32_t)i;
-        }
+        std::vector<int64_t> pos(RBFFD_MAX_N + 1, 0);   // next row of each stencil size
+        for (int g = 0; g < gi.ngroups; ++g) pos[gi.n[g]] = gi.row_begin[g];
+        for (int64_t i = 0; i < N; ++i) rn[pos[hn[i]]++] = (int32_t)i;
         TRY_OP(cudaMemcpyAsync(op->row_node, rn.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         TRY_OP(cudaStreamSynchronize(st));
     } else {
