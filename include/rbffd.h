@@ -427,6 +427,31 @@ rbffd_status rbffd_mlp_predict(const rbffd_mlp* mlp, const float* feats, int64_t
  */
 rbffd_status rbffd_selftest_barrier_timeout(void* stream);
 
+/*
+ * Transient device memory.  The scratch that calls need only while they run
+ * (the search's per-lane matrices -- about 13 GB for a 1M-node build with
+ * stencils up to n = 104 at the default launch shape -- the kNN grid, the
+ * learned guesses, ...) comes from a stream-ordered memory pool that the
+ * library owns, one per device, and goes back to it in stream order when the
+ * call's work is done.  The pool keeps up to keep_bytes of that memory
+ * mapped between calls (default 32 GiB), so that the next build does not map
+ * it again; the rest is returned to the device at the next synchronisation.
+ * Operators, ELL arrays and stepping workspaces are ordinary allocations
+ * owned by the operator, not pool memory.
+ *
+ * rbffd_memory_pool_config: sets keep_bytes for the current device's pool
+ *   (>= 0; 0 returns everything at each synchronisation).
+ * rbffd_release_memory: returns all pool memory that no call is using to
+ *   the device now (after the calls' streams have been synchronised).
+ * rbffd_memory_stats: bytes the current device's pool holds mapped and
+ *   bytes in use by calls in flight (either pointer may be NULL).
+ * Errors: RBFFD_EINVAL for keep_bytes < 0, RBFFD_ECUDA when the pool cannot
+ * be created or queried.
+ */
+rbffd_status rbffd_memory_pool_config(int64_t keep_bytes);
+rbffd_status rbffd_release_memory(void);
+rbffd_status rbffd_memory_stats(int64_t* reserved, int64_t* used);
+
 /* ------------------------------------------------------------------------ */
 const char* rbffd_status_str(rbffd_status s);
 const char* rbffd_last_error(void);

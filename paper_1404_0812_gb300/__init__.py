@@ -379,6 +379,24 @@ def fp64_peak(stream=None) -> float:
     return g.value
 
 
+def memory_pool_config(keep_bytes: int) -> None:
+    """rbffd_memory_pool_config: bytes of transient scratch the library's
+    pool keeps mapped between calls on the current device."""
+    _lib.check(_lib.load().rbffd_memory_pool_config(int(keep_bytes)), "rbffd_memory_pool_config")
+
+
+def release_memory() -> None:
+    """rbffd_release_memory: return the pool's unused memory to the device."""
+    _lib.check(_lib.load().rbffd_release_memory(), "rbffd_release_memory")
+
+
+def memory_stats() -> dict:
+    """rbffd_memory_stats: {"reserved": bytes mapped, "used": bytes in use}."""
+    r, u = C.c_int64(), C.c_int64()
+    _lib.check(_lib.load().rbffd_memory_stats(C.byref(r), C.byref(u)), "rbffd_memory_stats")
+    return {"reserved": r.value, "used": u.value}
+
+
 def selftest_barrier_timeout(stream=None) -> int:
     """rbffd_selftest_barrier_timeout; returns the status (TIMEOUT expected)."""
     return int(_lib.load().rbffd_selftest_barrier_timeout(_stream(stream)))

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <map>
@@ -23,6 +24,49 @@ void set_error(const char* fmt, ...) {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int k) { g_launches.fetch_add(k); }
+
+// ---- the library's stream-ordered memory pools (one per device)
+namespace {
+constexpr int MAX_DEVICES = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[MAX_DEVICES] = {};
+constexpr uint64_t POOL_KEEP_DEFAULT = 32ull << 30;
+
+cudaError_t device_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = POOL_KEEP_DEFAULT;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t pool_alloc_bytes(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 
 int sm_count() {
     int dev = 0, n = 0;
@@ -83,7 +127,7 @@ __global__ void rows_kernel(const int32_t* __restrict__ idx, const double* __res
 // (synchronises the stream)
 cudaError_t failed_stencils(const rbffd_op* op, cudaStream_t st, int* count) {
     int* bad = nullptr;
-    cudaError_t e = cudaMallocAsync(&bad, sizeof(int), st);
+    cudaError_t e = pool_alloc(&bad, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
     if (e == cudaSuccess) {
         count_status<<<(unsigned)((op->N + 255) / 256), 256, 0, st>>>(op->status, op->N, bad);
@@ -276,7 +320,7 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     if (!o.eps_override) {
         float* guess = nullptr;
         if (o.use_learned) {
-            TRY_OP(cudaMallocAsync(&guess, N * sizeof(float), st));
+            TRY_OP(pool_alloc(&guess, N * sizeof(float), st));
             s = mlp_guess(op, nodes, normals, o, guess, st);
             if (s != RBFFD_OK) {
                 cudaFreeAsync(guess, st);
@@ -401,3 +445,30 @@ int64_t rbffd_op_apply_bytes(const rbffd_op* op, int dtype) {
 void rbffd_destroy(rbffd_op* op) { free_op(op); }
 
 }  // extern "C"
+
+extern "C" rbffd_status rbffd_memory_pool_config(int64_t keep_bytes) {
+    RBFFD_CHECK_ARG(keep_bytes >= 0, "keep_bytes must be >= 0");
+    cudaMemPool_t pool = nullptr;
+    RBFFD_CUDA_TRY(device_pool(&pool));
+    uint64_t keep = (uint64_t)keep_bytes;
+    RBFFD_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    return RBFFD_OK;
+}
+
+extern "C" rbffd_status rbffd_release_memory(void) {
+    cudaMemPool_t pool = nullptr;
+    RBFFD_CUDA_TRY(device_pool(&pool));
+    RBFFD_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+    return RBFFD_OK;
+}
+
+extern "C" rbffd_status rbffd_memory_stats(int64_t* reserved, int64_t* used) {
+    cudaMemPool_t pool = nullptr;
+    RBFFD_CUDA_TRY(device_pool(&pool));
+    uint64_t r = 0, u = 0;
+    RBFFD_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    RBFFD_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    if (reserved) *reserved = (int64_t)r;
+    if (used) *used = (int64_t)u;
+    return RBFFD_OK;
+}

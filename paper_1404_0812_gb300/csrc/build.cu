@@ -15,8 +15,10 @@
 // Eq. rbf_linsys): Phi is positive definite for the Gaussian and IMQ
 // kernels, so A = [[Phi, 1], [1^T, 0]] is solved through Phi = L L^T and
 // its Schur complement s = 1^T Phi^{-1} 1.  max|lambda(A)| comes from a
-// short Lanczos run with A (A x formed as L (L^T x) plus the border), and
-// 1 / min|lambda(A)| from a short Lanczos run with A^{-1}; each run stops
+// short Lanczos run with A in float32 (on a float32 copy of Phi: the
+// dominant eigenvalue is well separated and well conditioned, and a
+// relative error of ~1e-6 in kappa moves the root by ~1e-7 in ln eps), and
+// 1 / min|lambda(A)| from a float64 Lanczos run with A^{-1}; each run stops
 // when its extreme Ritz value settles (relative change 1e-6).  The Ritz
 // values of the small tridiagonal are found by Sturm-count bisection in
 // float32 (relative accuracy ~1e-7, far below the float64 noise of kappa).
@@ -69,19 +71,35 @@ struct Lane {
     __device__ __forceinline__ double& operator[](int e) const { return p[(int64_t)e * 32]; }
 };
 
+// float32 view of a region of the same scratch: float element e of this lane
+// lies at e * 32 + lane floats from the region's start (region start R in
+// double units per lane = R * 32 doubles from the warp's base), so a region
+// of k doubles per lane holds 2k floats per lane, again one coalesced
+// transaction per warp access.
+struct LaneF {
+    float* p;
+    __device__ __forceinline__ float& operator[](int e) const { return p[(int64_t)e * 32]; }
+};
+
+__device__ __forceinline__ LaneF float_view(const Lane& S, int region) {
+    const int lane = threadIdx.x & 31;
+    return LaneF{reinterpret_cast<float*>(S.p - lane + (int64_t)region * 32) + lane};
+}
+
 __host__ __device__ inline int pk(int i, int j) { return i * (i + 1) / 2 + j; }
 
 struct Layout {
     int m;       // padded stencil size (multiple of 4)
     int P;       // m (m + 1) / 2
-    int R2, L, PH, XS, NS, U, ID, Q0, Q1, Q2, T0, GV, HV, QB, RV;
+    int R2, L, PH, XS, NS, U, ID, Q0, Q2, GV, HV, QB, RV;
+    int PF, FV;  // float32 regions (search only): copy of Phi, three Lanczos vectors
     int size;    // doubles per lane
 };
 
 // full = true: the weights kernel's layout; full = false: the search's, which
-// adds the Lanczos basis and the Ritz vector kept between evaluations (both
-// hold the Phi copy, normals and gradient vectors: the search computes the
-// weights from its last factorisation).
+// adds the Lanczos basis, the Ritz vector and the float32 regions of the
+// lambda_max run (both hold the Phi copy, normals and gradient vectors: the
+// search computes the weights from its last factorisation).
 __host__ __device__ inline Layout make_layout(int m, bool full) {
     Layout l;
     l.m = m;
@@ -94,16 +112,16 @@ __host__ __device__ inline Layout make_layout(int m, bool full) {
     l.U = o; o += m;
     l.ID = o; o += m;
     l.Q0 = o; o += m;
-    l.Q1 = o; o += m;
     l.Q2 = o; o += m;
-    l.T0 = o; o += m;
     l.NS = o; o += 3 * m;
     l.GV = o; o += 3 * m;
     l.HV = o; o += 3 * m;
-    l.QB = l.RV = -1;
+    l.QB = l.RV = l.PF = l.FV = -1;
     if (!full) {
         l.QB = o; o += LANCZOS_KMAX * m;   // Lanczos basis
         l.RV = o; o += m;
+        l.PF = o; o += (l.P + 1) / 2;      // P floats
+        l.FV = o; o += (3 * m + 1) / 2;    // 3 m floats
     }
     l.size = o;
     return l;
@@ -176,10 +194,11 @@ __device__ Geo load_geometry(const Lane& S, const Layout& ly, int n, const int32
 }
 
 // Phi(eps) into region dst (lower packed, m x m, identity on the padding);
-// optionally a copy into region cpy.
+// optionally a copy into region cpy and a float32 copy into region fcpy.
 __device__ void assemble_phi(const Lane& S, const Layout& ly, int n, int kernel, double eps_s,
-                             int dst, int cpy) {
+                             int dst, int cpy, int fcpy = -1) {
     double e2 = eps_s * eps_s;
+    const LaneF F = float_view(S, fcpy >= 0 ? fcpy : 0);
     for (int i = 0; i < ly.m; ++i) {
         int base = pk(i, 0);
         if (i < n) {
@@ -187,15 +206,18 @@ __device__ void assemble_phi(const Lane& S, const Layout& ly, int n, int kernel,
                 double v = phi_of(kernel, e2 * S[ly.R2 + base + j]);
                 S[dst + base + j] = v;
                 if (cpy >= 0) S[cpy + base + j] = v;
+                if (fcpy >= 0) F[base + j] = (float)v;
             }
         } else {
             for (int j = 0; j < i; ++j) {
                 S[dst + base + j] = 0.0;
                 if (cpy >= 0) S[cpy + base + j] = 0.0;
+                if (fcpy >= 0) F[base + j] = 0.f;
             }
         }
         S[dst + base + i] = 1.0;
         if (cpy >= 0) S[cpy + base + i] = 1.0;
+        if (fcpy >= 0) F[base + i] = 1.f;
     }
 }
 
@@ -340,34 +362,6 @@ __device__ void chol_solve(const Lane& S, const Layout& ly, int V) {
     }
 }
 
-// y <- Phi x = L (L^T x); x in region VX, y in region VY (distinct), uses T0.
-__device__ void chol_mul(const Lane& S, const Layout& ly, int VX, int VY) {
-    const int m = ly.m, L = ly.L, T = ly.T0;
-    for (int i = 0; i < m; ++i) S[T + i] = 0.0;
-    // t = L^T x : t_i += L(k, i) x_k
-    for (int k = 0; k < m; ++k) {
-        double xk = S[VX + k];
-        int r = pk(k, 0);
-        for (int i = 0; i <= k; ++i) S[T + i] = fma(S[L + r + i], xk, S[T + i]);
-    }
-    // y = L t, four rows at a time (independent accumulators)
-    for (int i = 0; i < m; i += 4) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        const int r = pk(i, 0);
-        for (int k = 0; k <= i; ++k) {
-            double tk = S[T + k];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fma(S[L + r + q * i + q * (q + 1) / 2 + k], tk, acc[q]);
-        }
-#pragma unroll
-        for (int q = 1; q < 4; ++q)
-#pragma unroll
-            for (int k = i + 1; k <= i + q; ++k) acc[q] = fma(S[L + r + q * i + q * (q + 1) / 2 + k], S[T + k], acc[q]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) S[VY + i + q] = acc[q];
-    }
-}
-
 // ---------------------------------------------------------------------------
 // extreme eigenvalues of a symmetric tridiagonal (float32 Sturm bisection)
 // ---------------------------------------------------------------------------
@@ -466,105 +460,126 @@ __device__ void tri_eigvec(const double* al, const double* be, int k, double the
     }
 }
 
-// Lanczos with op = A^{-1} (inv = true) or A (inv = false) on augmented
-// vectors (m entries in a region + one border scalar).  Returns the extreme
-// |Ritz value|.  Requires L, ID, U (Phi^{-1} 1) and s.
-__device__ double lanczos_extreme(const Lane& S, const Layout& ly, int n, bool inv, double s,
-                                  double rtol) {
+// y = Phi x in float32 from the packed float32 copy F of Phi, x and y at
+// float offsets x, y of V.  Rows in blocks of four (four independent FMA
+// chains; each x_j loaded once per block): columns left of the block from
+// the block's rows, the 4 x 4 diagonal block, and columns right of it from
+// the rows below (symmetry).  The padding rows of Phi are the identity and
+// entries n..m-1 of x are zero, so the loops run to m.
+__device__ void phi_mul_f32(const LaneF& F, const LaneF& V, int x, int y, int m) {
+    for (int ib = 0; ib < m; ib += 4) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int r = pk(ib, 0);   // row ib + a starts at r + a ib + a (a + 1) / 2
+        for (int j = 0; j < ib; ++j) {
+            const float xj = V[x + j];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = fmaf(F[r + a * ib + a * (a + 1) / 2 + j], xj, acc[a]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float xc = V[x + ib + c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                acc[a] = fmaf(F[a >= c ? pk(ib + a, ib + c) : pk(ib + c, ib + a)], xc, acc[a]);
+        }
+        for (int j = ib + 4; j < m; ++j) {
+            const float xj = V[x + j];
+            const int rj = pk(j, ib);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = fmaf(F[rj + a], xj, acc[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) V[y + ib + a] = acc[a];
+    }
+}
+
+// max|lambda(A)| of A = [[Phi, 1], [1^T, 0]] by Lanczos in float32 on the
+// float32 copy of Phi (region PF, written by assemble_phi) with vectors in
+// region FV (m entries each plus a border scalar).  The start vector is
+// mostly the constant vector, close to the dominant eigenvector when Phi is
+// nearly flat (Phi ~ 1 1^T), plus a 1 % oscillation so that no eigenvector
+// is missed; two steps can then settle.  The dominant eigenvalue is well
+// conditioned (Weyl: float32 rounding of Phi and of the products moves it
+// by ~sqrt(m) 6e-8 relative), so float32 costs kappa no accuracy that the
+// root finder would notice and takes the run off the float64 pipe.
+__device__ double lanczos_max_f32(const Lane& S, const Layout& ly, int n, double rtol) {
     const int m = ly.m;
+    const LaneF F = float_view(S, ly.PF), V = float_view(S, ly.FV);
     float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
     double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX];
-    int qp = ly.Q0, q_ = ly.Q1, w = ly.Q2;
-    // start vector.  For A^{-1}: cos(1.7 i + 0.3) + 0.1 on the n nodes and the
-    // border (no preferred direction).  For A: mostly the constant vector,
-    // close to the dominant eigenvector when Phi is nearly flat (Phi ~ 1 1^T),
-    // plus the same oscillation at 1% so no eigenvector is missed.
-    double nrm2 = 0.0;
+    int qp = 0, q_ = m, w = 2 * m;
+    float nrm2 = 0.f;
     for (int i = 0; i < m; ++i) {
-        double osc = cos(1.7 * i + 0.3) + 0.1;
-        double v = i < n ? (inv ? osc : 1.0 + 0.01 * osc) : 0.0;
-        S[q_ + i] = v;
-        S[qp + i] = 0.0;
-        nrm2 += v * v;
+        const float v = i < n ? 1.0f + 0.01f * (__cosf(1.7f * (float)i + 0.3f) + 0.1f) : 0.f;
+        V[q_ + i] = v;
+        V[qp + i] = 0.f;
+        nrm2 = fmaf(v, v, nrm2);
     }
-    double qb = inv ? cos(1.7 * n + 0.3) + 0.1 : 0.1, qpb = 0.0;
-    nrm2 += qb * qb;
-    double inrm = rsqrt(nrm2);
-    for (int i = 0; i < n; ++i) S[q_ + i] *= inrm;
+    float qb = 0.1f, qpb = 0.f;
+    nrm2 = fmaf(qb, qb, nrm2);
+    const float inrm = rsqrtf(nrm2);
+    for (int i = 0; i < n; ++i) V[q_ + i] *= inrm;
     qb *= inrm;
-    double beta = 0.0, prev = -1.0, ext = 0.0;
+    float beta = 0.f;
+    double prev = -1.0, ext = 0.0;
     for (int j = 0; j < LANCZOS_KMAX; ++j) {
-        double wb;
-        if (inv) {
-            // [c; d] = A^{-1} [f; g]: c0 = Phi^{-1} f, d = (1^T c0 - g) / s, c = c0 - d u
-            for (int i = 0; i < m; ++i) S[w + i] = S[q_ + i];
-            chol_solve(S, ly, w);
-            double sum = 0.0;
-            for (int i = 0; i < n; ++i) sum += S[w + i];
-            double d = (sum - qb) / s;
-            for (int i = 0; i < n; ++i) S[w + i] = fma(-d, S[ly.U + i], S[w + i]);
-            wb = d;
-        } else {
-            chol_mul(S, ly, q_, w);
-            double sum = 0.0;
-            for (int i = 0; i < n; ++i) {
-                sum += S[q_ + i];
-                S[w + i] += qb;
-            }
-            wb = sum;
+        // [Phi q + qb 1; 1^T q]
+        phi_mul_f32(F, V, q_, w, m);
+        float sum = 0.f;
+        for (int i = 0; i < n; ++i) {
+            sum += V[q_ + i];
+            V[w + i] += qb;
         }
-        // four partial sums keep independent FMA chains in flight; entries
-        // n..m-1 of every vector are zero, so the loops run to m
-        double ap[4] = {0.0, 0.0, 0.0, 0.0};
+        float wb = fmaf(-beta, qpb, sum);
+        float ap[4] = {0.f, 0.f, 0.f, 0.f};
         for (int i = 0; i < m; i += 4) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                double v = fma(-beta, S[qp + i + q], S[w + i + q]);
-                S[w + i + q] = v;
-                ap[q] = fma(S[q_ + i + q], v, ap[q]);
+                const float v = fmaf(-beta, V[qp + i + q], V[w + i + q]);
+                V[w + i + q] = v;
+                ap[q] = fmaf(V[q_ + i + q], v, ap[q]);
             }
         }
-        wb = fma(-beta, qpb, wb);
-        double a = fma(qb, wb, (ap[0] + ap[1]) + (ap[2] + ap[3]));
-        double bp[4] = {0.0, 0.0, 0.0, 0.0};
+        const float a = fmaf(qb, wb, (ap[0] + ap[1]) + (ap[2] + ap[3]));
+        float bp[4] = {0.f, 0.f, 0.f, 0.f};
         for (int i = 0; i < m; i += 4) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                double v = fma(-a, S[q_ + i + q], S[w + i + q]);
-                S[w + i + q] = v;
-                bp[q] = fma(v, v, bp[q]);
+                const float v = fmaf(-a, V[q_ + i + q], V[w + i + q]);
+                V[w + i + q] = v;
+                bp[q] = fmaf(v, v, bp[q]);
             }
         }
-        double bn = (bp[0] + bp[1]) + (bp[2] + bp[3]);
-        wb = fma(-a, qb, wb);
-        bn = sqrt(fma(wb, wb, bn));
+        wb = fmaf(-a, qb, wb);
+        const float bn = sqrtf(fmaf(wb, wb, (bp[0] + bp[1]) + (bp[2] + bp[3])));
         alpha_d[j] = a;
         beta_d[j] = bn;
-        // scaled tridiagonal in float32 (Gershgorin bound as the scale)
+        // scaled tridiagonal (Gershgorin bound as the scale)
         double G = 0.0;
         for (int i = 0; i <= j; ++i) {
             double r = fabs(alpha_d[i]) + (i < j ? beta_d[i] : 0.0) + (i > 0 ? beta_d[i - 1] : 0.0);
             G = fmax(G, r);
         }
-        double ig = 1.0 / G;
+        const double ig = 1.0 / G;
         for (int i = 0; i <= j; ++i) {
             al[i] = (float)(alpha_d[i] * ig);
-            float bb = (float)(beta_d[i] * ig);
+            const float bb = (float)(beta_d[i] * ig);
             b2[i] = bb * bb;
         }
         ext = tri_max_abs(al, b2, j + 1, G);
-        // the A run starts next to its dominant eigenvector: two steps can settle
-        if (j + 1 >= (inv ? LANCZOS_KMIN : 2) && fabs(ext - prev) <= rtol * ext) break;
-        if (bn <= 1e-14 * fabs(a)) break;
+        if (j + 1 >= 2 && fabs(ext - prev) <= rtol * ext) break;
+        // an invariant subspace to float32 precision: the residual bounds the
+        // error of the Ritz value by bn
+        if (bn <= 1e-6f * fabsf(a)) break;
         prev = ext;
         beta = bn;
-        double ib = 1.0 / bn;
-        int t = qp;
+        const float ib = 1.f / bn;
+        const int t = qp;
         qp = q_;
         q_ = w;
         w = t;
         qpb = qb;
-        for (int i = 0; i < n; ++i) S[q_ + i] *= ib;
+        for (int i = 0; i < n; ++i) V[q_ + i] *= ib;
         qb = wb * ib;
     }
     return ext;
@@ -723,7 +738,7 @@ __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel,
     double* dF = theta_out;
     *dF = NAN;
     *schur = 0.0;
-    assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH);
+    assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH, ly.PF);
     if (!cholesky(S, ly)) return INFINITY;
     for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
     chol_solve(S, ly, ly.U);
@@ -732,7 +747,7 @@ __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel,
     if (!(s > 0.0)) return INFINITY;
     *schur = s;
     double theta = lanczos_inv_ritz(S, ly, n, s, LANCZOS_RTOL, warm, vb, seed);
-    double lmax = lanczos_extreme(S, ly, n, false, s, LANCZOS_RTOL);
+    double lmax = lanczos_max_f32(S, ly, n, LANCZOS_RTOL);
     double k = lmax * fabs(theta);
     if (!isfinite(k)) return INFINITY;
     *dF = theta;   // the caller turns it into dF/dx with kappa_slope() when needed
@@ -1167,8 +1182,8 @@ rbffd_status build_search(rbffd_op* op, const double* nodes, const double* norma
     int64_t lanes = (int64_t)ls.blocks * ls.threads;
     double* scratch = nullptr;
     unsigned long long* ctr = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&scratch, (size_t)lanes * ly.size * sizeof(double), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&ctr, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
+    RBFFD_CUDA_TRY(pool_alloc(&scratch, (size_t)lanes * ly.size * sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&ctr, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(ctr, 0, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
     SearchArgs A;
     A.X = nodes;
@@ -1213,8 +1228,8 @@ rbffd_status build_weights(rbffd_op* op, const double* nodes, const double* norm
     int64_t lanes = (int64_t)ls.blocks * ls.threads;
     double* scratch = nullptr;
     int* nfail = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&scratch, (size_t)lanes * ly.size * sizeof(double), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&nfail, sizeof(int), st));
+    RBFFD_CUDA_TRY(pool_alloc(&scratch, (size_t)lanes * ly.size * sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&nfail, sizeof(int), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(nfail, 0, sizeof(int), st));
     WeightArgs A;
     A.X = nodes;
@@ -1966,8 +1981,8 @@ rbffd_status build_search_dd(rbffd_op* op, const double* nodes, const double* no
     const int64_t lanes = (int64_t)blocks * threads;
     double* scratch = nullptr;
     unsigned long long* ctr = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&scratch, (size_t)lanes * ly.size * 2 * sizeof(double), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&ctr, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
+    RBFFD_CUDA_TRY(pool_alloc(&scratch, (size_t)lanes * ly.size * 2 * sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&ctr, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(ctr, 0, RBFFD_MAX_GROUPS * sizeof(unsigned long long), st));
     SearchDDArgs D;
     SearchArgs& A = D.a;

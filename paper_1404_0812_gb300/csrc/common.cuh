@@ -40,6 +40,14 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // count of kernel launches issued by the library (reported to callers)
 void note_launch(int k = 1);
 
+// transient device memory from the library's per-device stream-ordered pool
+// (kept mapped between calls up to a threshold); free with cudaFreeAsync
+cudaError_t pool_alloc_bytes(void** p, size_t bytes, cudaStream_t st);
+template <typename T>
+inline cudaError_t pool_alloc(T** p, size_t bytes, cudaStream_t st) {
+    return pool_alloc_bytes(reinterpret_cast<void**>(p), bytes, st);
+}
+
 // ---------------------------------------------------------------------------
 // sliced ELL layout.  Rows are grouped by stencil size; within a group rows
 // are cut into slices of 32 consecutive rows, and each row's entries are

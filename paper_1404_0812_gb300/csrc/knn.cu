@@ -115,8 +115,8 @@ __global__ void scan_add(int32_t* __restrict__ out, int64_t n, const int32_t* __
 rbffd_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
     int64_t nb = (n + SCAN_T - 1) / SCAN_T;
     int32_t *bs = nullptr, *bo = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&bs, nb * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&bo, nb * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&bs, nb * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&bo, nb * sizeof(int32_t), st));
     scan_block<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, bs);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
@@ -313,8 +313,8 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     int nb = (int)std::min<int64_t>(1024, (N + BB_THREADS - 1) / BB_THREADS);
     double* part = nullptr;
     double* bb_d = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&part, (size_t)nb * 6 * sizeof(double), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&bb_d, 7 * sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&part, (size_t)nb * 6 * sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&bb_d, 7 * sizeof(double), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(bb_d + 6, 0, sizeof(int), st));
     bbox_partial<<<nb, BB_THREADS, 0, st>>>(nodes, normals, N, part, reinterpret_cast<int*>(bb_d + 6));
     note_launch();
@@ -368,15 +368,15 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     float4* sxf = nullptr;
     int32_t* node_row = nullptr;
     int* err = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&cell, N * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&count, (total + 1) * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&start, (total + 1) * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&cursor, total * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&sidx, N * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&sx, N * 3 * sizeof(double), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&sxf, N * sizeof(float4), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&node_row, N * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&err, sizeof(int), st));
+    RBFFD_CUDA_TRY(pool_alloc(&cell, N * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&count, (total + 1) * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&start, (total + 1) * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&cursor, total * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&sidx, N * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&sx, N * 3 * sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&sxf, N * sizeof(float4), st));
+    RBFFD_CUDA_TRY(pool_alloc(&node_row, N * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&err, sizeof(int), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(count, 0, (total + 1) * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(cursor, 0, total * sizeof(int32_t), st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));

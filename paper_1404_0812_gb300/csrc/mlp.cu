@@ -367,8 +367,8 @@ rbffd_status mlp_guess(const rbffd_op* op, const double* nodes, const double* no
         if (!net) continue;
         int64_t count = op->gi.row_begin[g + 1] - op->gi.row_begin[g];
         float *feats = nullptr, *pred = nullptr;
-        RBFFD_CUDA_TRY(cudaMallocAsync(&feats, count * net->D * sizeof(float), st));
-        RBFFD_CUDA_TRY(cudaMallocAsync(&pred, count * sizeof(float), st));
+        RBFFD_CUDA_TRY(pool_alloc(&feats, count * net->D * sizeof(float), st));
+        RBFFD_CUDA_TRY(pool_alloc(&pred, count * sizeof(float), st));
         features_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
             nodes, normals, op->idx, op->row_node, op->gi, g, nullptr, feats, nullptr);
         note_launch();
@@ -504,7 +504,7 @@ rbffd_status rbffd_mlp_train(rbffd_mlp* m, const float* feats, const float* targ
     s = ensure_smem(m->D);
     if (s != RBFFD_OK) return s;
     int32_t* perm_d = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&perm_d, count * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&perm_d, count * sizeof(int32_t), st));
     std::vector<int32_t> perm(count);
     for (int64_t i = 0; i < count; ++i) perm[i] = (int32_t)i;
     std::mt19937_64 rng(seed);

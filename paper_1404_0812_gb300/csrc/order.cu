@@ -90,7 +90,7 @@ extern "C" rbffd_status rbffd_morton_order(const double* nodes, int64_t N, int32
     const int nb = (int)std::min<int64_t>(1024, (N + 127) / 128);
     double* part = nullptr;
     uint64_t* key = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&part, (size_t)nb * 6 * sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&part, (size_t)nb * 6 * sizeof(double), st));
     bbox_blocks<<<nb, 128, 0, st>>>(nodes, N, part);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
@@ -107,7 +107,7 @@ extern "C" rbffd_status rbffd_morton_order(const double* nodes, int64_t N, int32
     double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
     RBFFD_CHECK_ARG(std::isfinite(ext), "non-finite node coordinates");
     const double scale = ext > 0.0 ? 2097151.0 / ext : 0.0;   // one cube: the Z-order keeps proportions
-    RBFFD_CUDA_TRY(cudaMallocAsync(&key, (size_t)N * sizeof(uint64_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&key, (size_t)N * sizeof(uint64_t), st));
     morton_keys<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(nodes, N, lo[0], lo[1], lo[2], scale, key);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
@@ -217,8 +217,8 @@ extern "C" rbffd_status rbffd_rcm_order(const rbffd_op* op, int32_t* perm, void*
     const int64_t N = op->N;
     const int nmax = op->n_max;
     int32_t *rows = nullptr, *deg = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&rows, (size_t)N * nmax * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(cudaMallocAsync(&deg, (size_t)N * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&rows, (size_t)N * nmax * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&deg, (size_t)N * sizeof(int32_t), st));
     stencil_rows<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(op->idx, op->row_node, op->gi, N, nmax, rows, deg);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());

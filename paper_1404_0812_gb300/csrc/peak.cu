@@ -27,7 +27,7 @@ extern "C" rbffd_status rbffd_fp64_peak(void* stream, double* gflops) {
     RBFFD_CHECK_ARG(gflops, "gflops is NULL");
     cudaStream_t st = as_stream(stream);
     double* out = nullptr;
-    RBFFD_CUDA_TRY(cudaMallocAsync(&out, sizeof(double), st));
+    RBFFD_CUDA_TRY(pool_alloc(&out, sizeof(double), st));
     const int threads = 256, blocks = sm_count() * 8, iters = 4096;
     cudaEvent_t e0, e1;
     RBFFD_CUDA_TRY(cudaEventCreate(&e0));

@@ -309,3 +309,32 @@ def test_invalid_options_are_rejected(R):
     with pytest.raises(R.RbffdError) as e:
         R.build_operator(X, Nr, 10, mlps=[net], accept=(2.0, 0.5))
     assert e.value.status == 1
+
+
+def test_memory_pool_keeps_and_releases_scratch(R):
+    """The build's transient scratch comes from the library's pool: all of it
+    is returned when the build is done, stays mapped for the next build
+    (which reuses it, dirty, with bit-identical results) and goes back to the
+    device on rbffd_release_memory."""
+    ns = W.fibonacci_sphere(20_000)
+    X, Nr = T(ns.X), T(ns.normals)
+    try:
+        R.memory_pool_config(32 << 30)
+        a = R.build_operator(X, Nr, 50, kernel="imq", kappa_target=1e12)
+        torch.cuda.synchronize()
+        st = R.memory_stats()
+        assert st["used"] == 0 and st["reserved"] > 0
+        b = R.build_operator(X, Nr, 50, kernel="imq", kappa_target=1e12)
+        torch.cuda.synchronize()
+        assert R.memory_stats()["reserved"] == st["reserved"]   # reused, not grown
+        ia, ib = R.get_stencil_info(a), R.get_stencil_info(b)
+        assert torch.equal(ia["eps"], ib["eps"]) and torch.equal(ia["kappa"], ib["kappa"])
+        ea, eb = R.get_ell(a), R.get_ell(b)
+        assert torch.equal(ea["w64"], eb["w64"])
+        R.release_memory()
+        assert R.memory_stats()["reserved"] == 0
+        with pytest.raises(R.RbffdError) as e:
+            R.memory_pool_config(-1)
+        assert e.value.status == 1
+    finally:
+        R.memory_pool_config(32 << 30)
