@@ -429,8 +429,8 @@ rbffd_status rbffd_selftest_barrier_timeout(void* stream);
 
 /*
  * Transient device memory.  The scratch that calls need only while they run
- * (the search's per-lane matrices -- about 13 GB for a 1M-node build with
- * stencils up to n = 104 at the default launch shape -- the kNN grid, the
+ * (the search's per-lane matrices -- about 15 GB for a 1M-node build with
+ * stencils up to n = 101 at the default launch shape -- the kNN grid, the
  * learned guesses, ...) comes from a stream-ordered memory pool that the
  * library owns, one per device, and goes back to it in stream order when the
  * call's work is done.  The pool keeps up to keep_bytes of that memory
