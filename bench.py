@@ -744,6 +744,7 @@ def run_ours(args):
     flops_at_E = sum(float(np.sum(nper == n)) * (E[int(n)] + 1.0) * (n + 1) ** 3 / 3.0 for n in SIZES)
     search_ms = statistics.mean(p["search"] for p in phases)
     peak = R.fp64_peak() / 1e3   # TFLOP/s, measured FMA throughput
+    peak_mma = R.fp64_mma_peak() / 1e3   # the FP64 tensor path, for comparison
     achieved = alg_flops_search / (search_ms * 1e-3) / 1e12
     traffic = SEARCH_TRAFFIC.get(_file_hash(os.path.join(ROOT, "paper_1404_0812_gb300", "csrc", "build.cu")))
     # apply bandwidth of the built operator (HBM; matrix far larger than L2)
@@ -807,6 +808,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "search_kernel (float64)", "achieved": round(achieved, 4),
                      "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "peak_source": "measured FP64 FMA microbenchmark (rbffd_fp64_peak)",
+                     "fp64_tensor_peak_measured": round(peak_mma, 4),
                      "traffic": traffic, "flops_per_launch": alg_flops_search,
                      "evals_mean_by_n": {int(n): round(float(ev_np[nper == n].mean()), 3) for n in SIZES},
                      "E_oracle_median": E, "search_ms": round(search_ms, 3),

@@ -458,6 +458,10 @@ const char* rbffd_last_error(void);
 /* Device FP64 FMA throughput microbenchmark (GFLOP/s, 2 flops per FMA),
  * used to report the build's roofline.  Synchronises the stream. */
 rbffd_status rbffd_fp64_peak(void* stream, double* gflops);
+/* Device FP64 tensor-path throughput microbenchmark (warp-level
+ * mma.sync m16n8k16 f64; GFLOP/s, 2 flops per multiply-add).  Synchronises
+ * the stream. */
+rbffd_status rbffd_fp64_mma_peak(void* stream, double* gflops);
 
 #ifdef __cplusplus
 }

@@ -397,6 +397,13 @@ def memory_stats() -> dict:
     return {"reserved": r.value, "used": u.value}
 
 
+def fp64_mma_peak(stream=None) -> float:
+    """FP64 tensor-path (mma.sync f64) throughput of this GPU in GFLOP/s."""
+    g = C.c_double()
+    _lib.check(_lib.load().rbffd_fp64_mma_peak(_stream(stream), C.byref(g)), "rbffd_fp64_mma_peak")
+    return g.value
+
+
 def selftest_barrier_timeout(stream=None) -> int:
     """rbffd_selftest_barrier_timeout; returns the status (TIMEOUT expected)."""
     return int(_lib.load().rbffd_selftest_barrier_timeout(_stream(stream)))

@@ -101,6 +101,7 @@ SIGNATURES = {
     "rbffd_status_str": (C.c_char_p, [C.c_int]),
     "rbffd_last_error": (C.c_char_p, []),
     "rbffd_fp64_peak": (C.c_int, [vp, C.POINTER(C.c_double)]),
+    "rbffd_fp64_mma_peak": (C.c_int, [vp, C.POINTER(C.c_double)]),
     "rbffd_memory_pool_config": (C.c_int, [C.c_int64]),
     "rbffd_release_memory": (C.c_int, []),
     "rbffd_memory_stats": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),

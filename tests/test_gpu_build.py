@@ -338,3 +338,9 @@ def test_memory_pool_keeps_and_releases_scratch(R):
         assert e.value.status == 1
     finally:
         R.memory_pool_config(32 << 30)
+
+
+def test_fp64_throughput_microbenchmarks(R):
+    """Both FP64 paths report a plausible rate for a GPU (GFLOP/s)."""
+    v, t = R.fp64_peak(), R.fp64_mma_peak()
+    assert 100.0 < v < 1e5 and 100.0 < t < 1e5, (v, t)
