@@ -10,7 +10,6 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
-#include <map>
 #include <string>
 #include <vector>
 
@@ -93,9 +92,13 @@ extern "C" rbffd_status rbffd_autotune_build(const double* nodes, const double* 
         std::vector<int32_t> hn(N);
         RBFFD_CUDA_TRY(cudaMemcpyAsync(hn.data(), n_per_node, N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
-        std::map<int, int> m;
-        for (int32_t v : hn) m[v] = 1;
-        for (auto& kv : m) sizes.push_back(kv.first);
+        std::vector<char> seen(RBFFD_MAX_N + 1, 0);
+        for (int32_t v : hn) {
+            RBFFD_CHECK_ARG(v >= 2 && v <= RBFFD_MAX_N, "stencil size must be in [2, 128]");
+            seen[v] = 1;
+        }
+        for (int v = 2; v <= RBFFD_MAX_N; ++v)
+            if (seen[v]) sizes.push_back(v);
     } else {
         sizes.push_back(n_uniform);
     }
