@@ -35,3 +35,15 @@ def test_status_strings_without_gpu():
     lib.rbffd_build_opts_default(ctypes.byref(o))
     assert o.kappa_target == 1e12 and o.eps_tol == 1e-4 and o.kernel == _lib.IMQ
     assert (o.accept_lo, o.accept_hi) == (0.5, 2.0)
+
+
+def test_argument_checks_need_no_gpu():
+    """Entry points validate their arguments before touching the device:
+    these return RBFFD_EINVAL (1) on a machine without a GPU."""
+    from paper_1404_0812_gb300 import _lib
+    lib = _lib.load()
+    assert lib.rbffd_memory_pool_config(-1) == _lib.EINVAL
+    assert lib.rbffd_fp64_peak(None, None) == _lib.EINVAL
+    assert lib.rbffd_fp64_mma_peak(None, None) == _lib.EINVAL
+    assert lib.rbffd_build_operator(None, None, 10, None, 5, None, None, None) == _lib.EINVAL
+    assert b"NULL" in lib.rbffd_last_error() or b"invalid" in lib.rbffd_last_error()
