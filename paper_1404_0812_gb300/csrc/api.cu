@@ -84,6 +84,81 @@ __global__ void iota_kernel(int32_t* a, int64_t n) {
     if (i < n) a[i] = (int32_t)i;
 }
 
+// ---- rows grouped by stencil size on the device: a counting sort by size,
+// stable in node order (rows of a group keep the nodes' order)
+constexpr int GROUP_CHUNK = 4096;   // nodes per block of the two grouping kernels
+constexpr int GROUP_THREADS = 256;
+
+// hist[v] = nodes with stencil size v (2 <= v <= RBFFD_MAX_N); sizes outside
+// that range are counted in hist[RBFFD_MAX_N + 1]
+__global__ void size_histogram(const int32_t* __restrict__ np, int64_t N, unsigned long long* __restrict__ hist) {
+    __shared__ unsigned int h[RBFFD_MAX_N + 2];
+    for (int i = threadIdx.x; i < RBFFD_MAX_N + 2; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = np[i];
+        atomicAdd(&h[(v >= 2 && v <= RBFFD_MAX_N) ? v : RBFFD_MAX_N + 1], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RBFFD_MAX_N + 2; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+struct SizeToGroup {
+    int8_t g[RBFFD_MAX_N + 1];   // group of each stencil size present
+};
+
+// counts[g * nchunks + c] = nodes of chunk c (GROUP_CHUNK consecutive nodes)
+// in group g
+__global__ void chunk_group_counts(const int32_t* __restrict__ np, int64_t N, SizeToGroup map, int G,
+                                   int64_t nchunks, int32_t* __restrict__ counts) {
+    __shared__ int cnt[RBFFD_MAX_GROUPS];
+    if (threadIdx.x < RBFFD_MAX_GROUPS) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t c = blockIdx.x;
+    const int64_t lo = c * GROUP_CHUNK, hi = min(N, lo + GROUP_CHUNK);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&cnt[map.g[np[i]]], 1);
+    __syncthreads();
+    if (threadIdx.x < G) counts[threadIdx.x * nchunks + c] = cnt[threadIdx.x];
+}
+
+// row_node[start[g * nchunks + c] + rank] = i, rank = the number of earlier
+// nodes of chunk c in group g (warp ballots, then warp totals in order)
+__global__ void __launch_bounds__(GROUP_THREADS)
+chunk_group_scatter(const int32_t* __restrict__ np, int64_t N, SizeToGroup map, int G, int64_t nchunks,
+                    const int32_t* __restrict__ start, int32_t* __restrict__ row_node) {
+    __shared__ int base[RBFFD_MAX_GROUPS];
+    __shared__ int wsum[GROUP_THREADS / 32][RBFFD_MAX_GROUPS];
+    const int64_t c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < G) base[threadIdx.x] = start[threadIdx.x * nchunks + c];
+    __syncthreads();
+    const int64_t lo = c * GROUP_CHUNK, hi = min(N, lo + GROUP_CHUNK);
+    for (int64_t i0 = lo; i0 < hi; i0 += GROUP_THREADS) {   // uniform across the block
+        const int64_t i = i0 + threadIdx.x;
+        const int g = i < hi ? map.g[np[i]] : -1;
+        int rank = 0;
+        for (int k = 0; k < G; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, g == k);
+            if (g == k) rank = __popc(m & ((1u << lane) - 1u));
+            if (lane == 0) wsum[warp][k] = __popc(m);
+        }
+        __syncthreads();
+        if (g >= 0) {
+            int off = base[g] + rank;
+            for (int w = 0; w < warp; ++w) off += wsum[w][g];
+            row_node[off] = (int32_t)i;
+        }
+        __syncthreads();
+        if (threadIdx.x < G) {
+            int tot = 0;
+            for (int w = 0; w < GROUP_THREADS / 32; ++w) tot += wsum[w][threadIdx.x];
+            base[threadIdx.x] += tot;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void init_info(double* eps, double* kappa, int32_t* evals, int32_t* status,
                           const double* eps_override, int64_t N) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -213,22 +288,24 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     cudaStream_t st = as_stream(stream);
 
     // ---- stencil-size groups (sorted by descending n; stable node order)
-    std::vector<int32_t> hn;
     std::map<int, int64_t> counts;
     if (n_per_node) {
-        hn.resize(N);
-        RBFFD_CUDA_TRY(cudaMemcpyAsync(hn.data(), n_per_node, N * sizeof(int32_t),
-                                       cudaMemcpyDeviceToHost, st));
-        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
-        // flat histogram over the admissible sizes (a map per node is slow at N = 1M)
-        std::vector<int64_t> hist(RBFFD_MAX_N + 1, 0);
-        for (int64_t i = 0; i < N; ++i) {
-            const int32_t v = hn[i];
-            RBFFD_CHECK_ARG(v >= 2 && v <= RBFFD_MAX_N, "stencil size must be in [2, 128]");
-            hist[v]++;
-        }
+        // histogram of the sizes on the device; only the 130 counts come back
+        unsigned long long* hist_d = nullptr;
+        unsigned long long hist[RBFFD_MAX_N + 2];
+        RBFFD_CUDA_TRY(pool_alloc(&hist_d, sizeof(hist), st));
+        RBFFD_CUDA_TRY(cudaMemsetAsync(hist_d, 0, sizeof(hist), st));
+        const int64_t hb = std::min<int64_t>((N + 255) / 256, (int64_t)sm_count() * 8);
+        size_histogram<<<(unsigned)hb, 256, 0, st>>>(n_per_node, N, hist_d);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hist, hist_d, sizeof(hist), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFreeAsync(hist_d, st);
+        RBFFD_CUDA_TRY(e);
+        RBFFD_CHECK_ARG(hist[RBFFD_MAX_N + 1] == 0, "stencil size must be in [2, 128]");
         for (int v = 2; v <= RBFFD_MAX_N; ++v)
-            if (hist[v]) counts[v] = hist[v];
+            if (hist[v]) counts[v] = (int64_t)hist[v];
     } else {
         counts[n_uniform] = N;
     }
@@ -285,12 +362,30 @@ rbffd_status rbffd_build_operator(const double* nodes, const double* normals, in
     TRY_OP(cudaMemsetAsync(op->w64, 0, op->ell_elems * sizeof(double), st));
     TRY_OP(cudaMemsetAsync(op->w32, 0, op->ell_elems * sizeof(float), st));
     if (n_per_node) {
-        std::vector<int32_t> rn(N);
-        std::vector<int64_t> pos(RBFFD_MAX_N + 1, 0);   // next row of each stencil size
-        for (int g = 0; g < gi.ngroups; ++g) pos[gi.n[g]] = gi.row_begin[g];
-        for (int64_t i = 0; i < N; ++i) rn[pos[hn[i]]++] = (int32_t)i;
-        TRY_OP(cudaMemcpyAsync(op->row_node, rn.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        TRY_OP(cudaStreamSynchronize(st));
+        SizeToGroup map;
+        memset(&map, -1, sizeof(map));
+        for (int g = 0; g < gi.ngroups; ++g) map.g[gi.n[g]] = (int8_t)g;
+        const int64_t nchunks = (N + GROUP_CHUNK - 1) / GROUP_CHUNK;
+        const int64_t ncnt = nchunks * gi.ngroups;
+        int32_t *cnt = nullptr, *start = nullptr;
+        TRY_OP(pool_alloc(&cnt, ncnt * sizeof(int32_t), st));
+        TRY_OP(pool_alloc(&start, ncnt * sizeof(int32_t), st));
+        chunk_group_counts<<<(unsigned)nchunks, GROUP_THREADS, 0, st>>>(n_per_node, N, map, gi.ngroups, nchunks,
+                                                                       cnt);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        rbffd_status rs = RBFFD_OK;
+        if (e == cudaSuccess) rs = exclusive_scan(cnt, start, ncnt, st);
+        if (e == cudaSuccess && rs == RBFFD_OK) {
+            chunk_group_scatter<<<(unsigned)nchunks, GROUP_THREADS, 0, st>>>(n_per_node, N, map, gi.ngroups,
+                                                                             nchunks, start, op->row_node);
+            note_launch();
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(cnt, st);
+        cudaFreeAsync(start, st);
+        TRY_OP(e);
+        if (rs != RBFFD_OK) return fail(rs);
     } else {
         iota_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(op->row_node, N);
         note_launch();

@@ -75,6 +75,9 @@ struct GroupInfo {
     int64_t ell_off[RBFFD_MAX_GROUPS + 1];     // element offsets
 };
 
+// exclusive prefix sum of n int32 values on the device (knn.cu)
+rbffd_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+
 __host__ __device__ inline int group_of_row(const GroupInfo& gi, int64_t r) {
     int g = 0;
     while (g + 1 < gi.ngroups && r >= gi.row_begin[g + 1]) ++g;

@@ -112,25 +112,6 @@ __global__ void scan_add(int32_t* __restrict__ out, int64_t n, const int32_t* __
     if (i < n) out[i] += block_off[blockIdx.x];
 }
 
-rbffd_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
-    int64_t nb = (n + SCAN_T - 1) / SCAN_T;
-    int32_t *bs = nullptr, *bo = nullptr;
-    RBFFD_CUDA_TRY(pool_alloc(&bs, nb * sizeof(int32_t), st));
-    RBFFD_CUDA_TRY(pool_alloc(&bo, nb * sizeof(int32_t), st));
-    scan_block<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, bs);
-    note_launch();
-    RBFFD_CUDA_TRY(cudaGetLastError());
-    if (nb > 1) {
-        rbffd_status r = exclusive_scan(bs, bo, nb, st);
-        if (r != RBFFD_OK) return r;
-        scan_add<<<(unsigned)nb, SCAN_T, 0, st>>>(out, n, bo);
-        note_launch();
-        RBFFD_CUDA_TRY(cudaGetLastError());
-    }
-    RBFFD_CUDA_TRY(cudaFreeAsync(bs, st));
-    RBFFD_CUDA_TRY(cudaFreeAsync(bo, st));
-    return RBFFD_OK;
-}
 
 __global__ void scatter_nodes(const double* __restrict__ X, int64_t N,
                               const int32_t* __restrict__ cell, const int32_t* __restrict__ start,
@@ -305,6 +286,28 @@ knn_query(const double* __restrict__ X, const int32_t* __restrict__ node_row, in
 }
 
 }  // namespace
+
+// Exclusive prefix sum of n int32 counts on the device (three-phase,
+// recursive over block sums); temporaries from the library's pool.
+rbffd_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
+    int64_t nb = (n + SCAN_T - 1) / SCAN_T;
+    int32_t *bs = nullptr, *bo = nullptr;
+    RBFFD_CUDA_TRY(pool_alloc(&bs, nb * sizeof(int32_t), st));
+    RBFFD_CUDA_TRY(pool_alloc(&bo, nb * sizeof(int32_t), st));
+    scan_block<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, bs);
+    note_launch();
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    if (nb > 1) {
+        rbffd_status r = exclusive_scan(bs, bo, nb, st);
+        if (r != RBFFD_OK) return r;
+        scan_add<<<(unsigned)nb, SCAN_T, 0, st>>>(out, n, bo);
+        note_launch();
+        RBFFD_CUDA_TRY(cudaGetLastError());
+    }
+    RBFFD_CUDA_TRY(cudaFreeAsync(bs, st));
+    RBFFD_CUDA_TRY(cudaFreeAsync(bo, st));
+    return RBFFD_OK;
+}
 
 rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* normals,
                           cudaStream_t st) {

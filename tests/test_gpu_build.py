@@ -344,3 +344,22 @@ def test_fp64_throughput_microbenchmarks(R):
     """Both FP64 paths report a plausible rate for a GPU (GFLOP/s)."""
     v, t = R.fp64_peak(), R.fp64_mma_peak()
     assert 100.0 < v < 1e5 and 100.0 < t < 1e5, (v, t)
+
+
+def test_rows_grouped_by_size_in_node_order(R):
+    """Rows are grouped by stencil size (largest first) and keep the nodes'
+    order inside a group, across many blocks of the device-side grouping
+    (60,000 nodes, sizes drawn at random per node)."""
+    ns = W.fibonacci_sphere(60_000)
+    rng = np.random.default_rng(7)
+    sizes = np.array([9, 21, 40, 64, 101])
+    nper = sizes[rng.integers(0, len(sizes), ns.N)].astype(np.int32)
+    eps = torch.full((ns.N,), 30.0, dtype=torch.float64, device="cuda")
+    op = R.build_operator(T(ns.X), T(ns.normals), T(nper, torch.int32), kernel="imq", eps_override=eps,
+                          allow_failures=True)
+    v = R.get_ell(op)
+    assert v["n"] == sorted(sizes.tolist(), reverse=True)
+    row_node = v["row_node"].cpu().numpy()
+    for g, n in enumerate(v["n"]):
+        rows = row_node[v["row_begin"][g]:v["row_begin"][g + 1]]
+        assert np.array_equal(rows, np.flatnonzero(nper == n))
