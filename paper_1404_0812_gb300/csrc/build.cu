@@ -966,7 +966,54 @@ __device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int ke
     }
     const int V = ly.Q0;
     for (int i = 0; i < m; ++i) S[V + i] = 0.0;
-    for (int i = 0; i < n; ++i) {
+    // pair (i, j), j < i: v_j += psi (x_i - x_j) . h_i ; v_i += psi (x_j - x_i) . h_j.
+    // Rows in blocks of four: x_j, h_j and v_j are loaded once per column for
+    // the four rows (a third of the scratch accesses of one row at a time).
+    // Every v_j still receives the rows' contributions in row order and every
+    // row sums its own in column order, so the result is the same bit for bit.
+    int i = 0;
+    for (; i + 4 <= n; i += 4) {
+        double xi[4], yi[4], zi[4], hx[4], hy[4], hz[4], vi[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            xi[a] = S[XS + i + a];
+            yi[a] = S[XS + m + i + a];
+            zi[a] = S[XS + 2 * m + i + a];
+            hx[a] = S[ly.HV + i + a];
+            hy[a] = S[ly.HV + m + i + a];
+            hz[a] = S[ly.HV + 2 * m + i + a];
+            vi[a] = 0.0;
+        }
+        const int r0 = pk(i, 0);   // row i + a starts at r0 + a i + a (a + 1) / 2
+        for (int j = 0; j < i; ++j) {
+            const double xj = S[XS + j], yj = S[XS + m + j], zj = S[XS + 2 * m + j];
+            const double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
+            double vj = S[V + j];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const double ps = psi_from_phi(kernel, e2, S[ly.PH + r0 + a * i + a * (a + 1) / 2 + j]);
+                const double dx = xi[a] - xj, dy = yi[a] - yj, dz = zi[a] - zj;
+                vj = fma(ps, dx * hx[a] + dy * hy[a] + dz * hz[a], vj);
+                vi[a] = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi[a]);
+            }
+            S[V + j] = vj;
+        }
+        // the pairs inside the block, row by row
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int c = 0; c < a; ++c) {
+                const int j = i + c;
+                const double ps = psi_from_phi(kernel, e2, S[ly.PH + pk(i + a, j)]);
+                const double dx = xi[a] - S[XS + j], dy = yi[a] - S[XS + m + j], dz = zi[a] - S[XS + 2 * m + j];
+                const double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
+                S[V + j] = fma(ps, dx * hx[a] + dy * hy[a] + dz * hz[a], S[V + j]);
+                vi[a] = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi[a]);
+            }
+            S[V + i + a] += vi[a];
+        }
+    }
+    for (; i < n; ++i) {
         double xi = S[XS + i], yi = S[XS + m + i], zi = S[XS + 2 * m + i];
         double hx = S[ly.HV + i], hy = S[ly.HV + m + i], hz = S[ly.HV + 2 * m + i];
         double vi = 0.0;
@@ -975,7 +1022,6 @@ __device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int ke
             double ps = psi_from_phi(kernel, e2, S[ly.PH + base + j]);
             double dx = xi - S[XS + j], dy = yi - S[XS + m + j], dz = zi - S[XS + 2 * m + j];
             double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
-            // pair (i, j): v_j += psi (x_i - x_j) . h_i ; v_i += psi (x_j - x_i) . h_j
             S[V + j] = fma(ps, dx * hx + dy * hy + dz * hz, S[V + j]);
             vi = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi);
         }
