@@ -57,9 +57,9 @@ UNIT = "stencils/s"
 # DRAM bytes per launch of the search kernel from one ncu capture, keyed by
 # the hash of build.cu at the time of the capture (None when not captured).
 # The capture ran the learned 160,000-node version of this workload (same four
-# stencil sizes, same networks): 216.13 GB read + 42.11 GB written; scaled to
+# stencil sizes, same networks): 204.02 GB read + 39.90 GB written; scaled to
 # the 1,000,000 stencils of one bench launch by the stencil count.
-SEARCH_TRAFFIC = {"3982e312ee49f7bd": (216.13e9 + 42.11e9) * 1_000_000 / 160_000}
+SEARCH_TRAFFIC = {"41fed6c06ba86a8d": (204.02e9 + 39.90e9) * 1_000_000 / 160_000}
 
 
 def _parse():
