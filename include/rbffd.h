@@ -119,7 +119,10 @@ rbffd_status rbffd_autotune_build(const double* nodes, const double* normals, in
  * F(eps) = ln(kappa_2(A_{P_k}(eps)) / kappa_T), Eq. target_cond, searched to
  * opts->eps_tol; Section 5) and the weights: the first row of
  * L_P = G^x G^x + G^y G^y + G^z G^z, G^d = B^d A^{-1} (Eqs. proj_mat,
- * grad_x_f_interp, surface_lap_P1).  All local linear algebra is float64.
+ * grad_x_f_interp, surface_lap_P1).  The local linear algebra is float64,
+ * except the short Lanczos estimate of max|lambda(A)| inside kappa_2, which
+ * runs in float32 (its relative error, ~1e-6, moves ln kappa by as much and
+ * eps_k by far less than eps_tol).
  *
  *   nodes      device, N x 3 float64, distinct points on the surface
  *   normals    device, N x 3 float64, unit normals (sign irrelevant)
