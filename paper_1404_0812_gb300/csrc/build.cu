@@ -221,87 +221,113 @@ __device__ void assemble_phi(const Lane& S, const Layout& ly, int n, int kernel,
     }
 }
 
+// acc[a][b] -= sum_{k < jb} L(ib + a, k) L(jb + b, k) for the first R rows
+// of the tile (software-pipelined: the loads of step k + 1 are in flight
+// while the 4 R FMAs of step k issue)
+template <int R>
+__device__ __forceinline__ void chol_tile_accumulate(const Lane& S, int L, int ib, int jb, double (&acc)[R][4]) {
+    const int ra = L + pk(ib, 0), rb = L + pk(jb, 0);
+    double xa[R], yb[4];
+#pragma unroll
+    for (int a = 0; a < R; ++a) xa[a] = S[ra + a * ib + a * (a + 1) / 2];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) yb[b] = S[rb + b * jb + b * (b + 1) / 2];
+    for (int k = 0; k < jb; ++k) {
+        double xn[R], yn[4];
+        const int kn = k + 1 < jb ? k + 1 : k;
+#pragma unroll
+        for (int a = 0; a < R; ++a) xn[a] = S[ra + a * ib + a * (a + 1) / 2 + kn];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) yn[b] = S[rb + b * jb + b * (b + 1) / 2 + kn];
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(-xa[a], yb[b], acc[a][b]);
+#pragma unroll
+        for (int a = 0; a < R; ++a) xa[a] = xn[a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) yb[b] = yn[b];
+    }
+}
+
+// Off-diagonal tile (ib > jb): rows ib .. ib + R - 1 of column block jb,
+// from the diagonal block's factor Ld and 1 / L_ii.  R < 4 only in the last
+// row block, whose other rows are padding (identity rows of Phi: their L
+// entries stay the zeros the assembly wrote, and no real row reads them).
+template <int R>
+__device__ __forceinline__ void chol_tile_offdiag(const Lane& S, const Layout& ly, int ib, int jb,
+                                                  const double (&Ld)[4][4]) {
+    const int L = ly.L;
+    double acc[R][4];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = S[L + pk(ib + a, jb + b)];
+    if (jb > 0) chol_tile_accumulate<R>(S, L, ib, jb, acc);
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            double v = acc[a][b];
+#pragma unroll
+            for (int c = 0; c < b; ++c) v = fma(-acc[a][c], Ld[b][c], v);
+            acc[a][b] = v * S[ly.ID + jb + b];
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) S[L + pk(ib + a, jb + b)] = acc[a][b];
+    }
+}
+
 // In-place packed Cholesky Phi = L L^T (left-looking, 4x4 register tiles).
-// ID receives 1 / L_ii.  Returns false when a pivot is not positive.
-__device__ bool cholesky(const Lane& S, const Layout& ly) {
+// ID receives 1 / L_ii.  Returns false when a pivot is not positive.  Rows
+// n .. m-1 are padding (identity in Phi and in L): the off-diagonal tiles of
+// the last row block leave them out.
+__device__ bool cholesky(const Lane& S, const Layout& ly, int n) {
     const int m = ly.m, L = ly.L;
     bool ok = true;
     for (int jb = 0; jb < m; jb += 4) {
         double Ld[4][4];
-        for (int ib = jb; ib < m; ib += 4) {
+        {
+            // diagonal block (all four rows, padding included: it sets 1 / L_ii = 1 there)
+            const int ib = jb;
             double acc[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    acc[a][b] = (ib + a >= jb + b) ? S[L + pk(ib + a, jb + b)] : 0.0;
-            if (jb > 0) {
-                // software-pipelined: the loads of step k + 1 are in flight
-                // while the 16 FMAs of step k issue
-                const int ra = L + pk(ib, 0), rb = L + pk(jb, 0);
-                double xa[4], yb[4];
+                for (int b = 0; b < 4; ++b) acc[a][b] = (a >= b) ? S[L + pk(ib + a, jb + b)] : 0.0;
+            if (jb > 0) chol_tile_accumulate<4>(S, L, ib, jb, acc);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) xa[a] = S[ra + a * ib + a * (a + 1) / 2];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) yb[b] = S[rb + b * jb + b * (b + 1) / 2];
-                for (int k = 0; k < jb; ++k) {
-                    double xn[4], yn[4];
-                    const int kn = k + 1 < jb ? k + 1 : k;
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) xn[a] = S[ra + a * ib + a * (a + 1) / 2 + kn];
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) yn[b] = S[rb + b * jb + b * (b + 1) / 2 + kn];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(-xa[a], yb[b], acc[a][b]);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        xa[a] = xn[a];
-                        yb[a] = yn[a];
-                    }
+            for (int b = 0; b < 4; ++b) {
+                double d = acc[b][b];
+                if (!(d > 0.0)) {
+                    ok = false;
+                    d = 1.0;
                 }
+                double l = sqrt(d);
+                double il = 1.0 / l;
+                acc[b][b] = l;
+                S[ly.ID + jb + b] = il;
+#pragma unroll
+                for (int a = b + 1; a < 4; ++a) acc[a][b] *= il;
+#pragma unroll
+                for (int c = b + 1; c < 4; ++c)
+#pragma unroll
+                    for (int a = c; a < 4; ++a) acc[a][c] = fma(-acc[a][b], acc[c][b], acc[a][c]);
             }
-            if (ib == jb) {
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    double d = acc[b][b];
-                    if (!(d > 0.0)) {
-                        ok = false;
-                        d = 1.0;
-                    }
-                    double l = sqrt(d);
-                    double il = 1.0 / l;
-                    acc[b][b] = l;
-                    S[ly.ID + jb + b] = il;
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int a = b + 1; a < 4; ++a) acc[a][b] *= il;
-#pragma unroll
-                    for (int c = b + 1; c < 4; ++c)
-#pragma unroll
-                        for (int a = c; a < 4; ++a) acc[a][c] = fma(-acc[a][b], acc[c][b], acc[a][c]);
+                for (int b = 0; b <= a; ++b) {
+                    Ld[a][b] = acc[a][b];
+                    S[L + pk(jb + a, jb + b)] = acc[a][b];
                 }
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b <= a; ++b) {
-                        Ld[a][b] = acc[a][b];
-                        S[L + pk(jb + a, jb + b)] = acc[a][b];
-                    }
-            } else {
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        double v = acc[a][b];
-#pragma unroll
-                        for (int c = 0; c < b; ++c) v = fma(-acc[a][c], Ld[b][c], v);
-                        acc[a][b] = v * S[ly.ID + jb + b];
-                    }
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) S[L + pk(ib + a, jb + b)] = acc[a][b];
-                }
-            }
+        }
+        for (int ib = jb + 4; ib < m; ib += 4) {
+            const int rows = n - ib;   // >= 1: padding is less than one block
+            if (rows >= 4) chol_tile_offdiag<4>(S, ly, ib, jb, Ld);
+            else if (rows == 3) chol_tile_offdiag<3>(S, ly, ib, jb, Ld);
+            else if (rows == 2) chol_tile_offdiag<2>(S, ly, ib, jb, Ld);
+            else chol_tile_offdiag<1>(S, ly, ib, jb, Ld);
         }
         if (!ok) return false;
     }
@@ -739,7 +765,7 @@ __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel,
     *dF = NAN;
     *schur = 0.0;
     assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH, ly.PF);
-    if (!cholesky(S, ly)) return INFINITY;
+    if (!cholesky(S, ly, n)) return INFINITY;
     for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
     chol_solve(S, ly, ly.U);
     double s = 0.0;
@@ -1170,7 +1196,7 @@ __global__ void __launch_bounds__(128, 4) weights_kernel(WeightArgs A) {
         int node = A.row_node[r];
         double eps_s = A.eps_node[node] * geo.rs;
         assemble_phi(S, ly, n, A.kernel, eps_s, ly.L, ly.PH);
-        bool ok = cholesky(S, ly) && isfinite(eps_s) && eps_s > 0.0;
+        bool ok = cholesky(S, ly, n) && isfinite(eps_s) && eps_s > 0.0;
         double s = 0.0;
         if (ok) {
             for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
@@ -1384,7 +1410,7 @@ weights_rows_kernel(const double* __restrict__ X, const double* __restrict__ NR,
         double s = 0.0;
         if (ok) {
             assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH);
-            ok = cholesky(S, ly) && isfinite(eps_s) && eps_s > 0.0;
+            ok = cholesky(S, ly, n) && isfinite(eps_s) && eps_s > 0.0;
         }
         if (ok) {
             for (int i = 0; i < m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
