@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 namespace rbffd {
@@ -126,46 +127,113 @@ extern "C" rbffd_status rbffd_morton_order(const double* nodes, int64_t N, int32
 extern "C" rbffd_status rbffd_rcm_order_host(const int64_t* rowptr, const int32_t* cols, int64_t N, int32_t* perm) {
     RBFFD_CHECK_ARG(rowptr && perm && (cols || N == 0), "NULL argument");
     RBFFD_CHECK_ARG(N >= 0 && N < (int64_t)1 << 31, "N must be in [0, 2^31)");
-    // symmetrised adjacency without self loops or repeats
-    std::vector<std::vector<int32_t>> adj((size_t)N);
     for (int64_t i = 0; i < N; ++i)
-        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-            int32_t j = cols[e];
-            RBFFD_CHECK_ARG(j >= 0 && j < N, "column index out of range");
-            if (j == i) continue;
-            adj[(size_t)i].push_back(j);
-            adj[(size_t)j].push_back((int32_t)i);
-        }
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+            RBFFD_CHECK_ARG(cols[e] >= 0 && cols[e] < N, "column index out of range");
+    // passes over disjoint ranges of nodes, on the host's cores
+    auto for_nodes = [&](auto&& body) {
+        const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), N / 4096));
+        std::vector<std::thread> pool;
+        for (int64_t t = 1; t < nt; ++t) pool.emplace_back([&, t] { body(N * t / nt, N * (t + 1) / nt); });
+        body(0, N / nt);
+        for (auto& th : pool) th.join();
+    };
+    // symmetrised adjacency in one flat array: node i's slots are
+    // nb[off[i] .. off[i + 1]) (its out- and in-edges, self loops dropped);
+    // after the repeats are removed its neighbours are the first deg[i].
+    // Each thread scans every edge and fills only the slots of its own
+    // nodes, so no two threads write the same place.
+    std::vector<int64_t> off((size_t)N + 1, 0);
+    for_nodes([&](int64_t lo, int64_t hi) {
+        for (int64_t i = 0; i < N; ++i)
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int64_t j = cols[e];
+                if (j == i) continue;
+                if (i >= lo && i < hi) off[(size_t)i + 1]++;
+                if (j >= lo && j < hi) off[(size_t)j + 1]++;
+            }
+    });
+    for (int64_t i = 0; i < N; ++i) off[(size_t)i + 1] += off[(size_t)i];
+    std::vector<int32_t> nb((size_t)off[(size_t)N]);
+    for_nodes([&](int64_t lo, int64_t hi) {
+        std::vector<int64_t> fill(off.begin() + lo, off.begin() + hi);
+        for (int64_t i = 0; i < N; ++i)
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int64_t j = cols[e];
+                if (j == i) continue;
+                if (i >= lo && i < hi) nb[(size_t)fill[(size_t)(i - lo)]++] = (int32_t)j;
+                if (j >= lo && j < hi) nb[(size_t)fill[(size_t)(j - lo)]++] = (int32_t)i;
+            }
+    });
     std::vector<int32_t> deg((size_t)N);
-    for (int64_t i = 0; i < N; ++i) {
-        auto& a = adj[(size_t)i];
-        std::sort(a.begin(), a.end());
-        a.erase(std::unique(a.begin(), a.end()), a.end());
-        deg[(size_t)i] = (int32_t)a.size();
-    }
-    // neighbours in increasing degree (ties by index), the Cuthill-McKee visiting order
-    for (int64_t i = 0; i < N; ++i)
-        std::sort(adj[(size_t)i].begin(), adj[(size_t)i].end(),
-                  [&](int32_t a, int32_t b) { return deg[a] < deg[b] || (deg[a] == deg[b] && a < b); });
+    for_nodes([&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            int32_t* a = nb.data() + off[(size_t)i];
+            int32_t* b = nb.data() + off[(size_t)i + 1];
+            std::sort(a, b);
+            deg[(size_t)i] = (int32_t)(std::unique(a, b) - a);
+        }
+    });
+    // neighbours in increasing degree (ties by index), the Cuthill-McKee
+    // visiting order: sorted as 64-bit keys (degree, index)
+    for_nodes([&](int64_t lo, int64_t hi) {
+        std::vector<uint64_t> key;
+        for (int64_t i = lo; i < hi; ++i) {
+            int32_t* a = nb.data() + off[(size_t)i];
+            const int32_t d = deg[(size_t)i];
+            key.resize((size_t)d);
+            for (int32_t k = 0; k < d; ++k) key[(size_t)k] = ((uint64_t)(uint32_t)deg[(size_t)a[k]] << 32) | (uint32_t)a[k];
+            std::sort(key.begin(), key.end());
+            for (int32_t k = 0; k < d; ++k) a[k] = (int32_t)(key[(size_t)k] & 0xffffffffu);
+        }
+    });
+    auto adj_begin = [&](int32_t v) { return nb.data() + off[(size_t)v]; };
+    auto adj_end = [&](int32_t v) { return nb.data() + off[(size_t)v] + deg[(size_t)v]; };
     std::vector<int32_t> level((size_t)N, -1), order;
     order.reserve((size_t)N);
     std::vector<char> done((size_t)N, 0);
     std::vector<int32_t> queue;
     queue.reserve((size_t)N);
-    // BFS from s over the unvisited component: levels and the last level
+    // BFS from s over the unvisited component: levels and the last level.
+    // Level-synchronous: each frontier (comp[fb, fe), all at level depth) is
+    // expanded by the host's threads, a node joining the next frontier through
+    // an atomic claim of its level.  Levels, depth and the component's node
+    // set are those of a sequential BFS; only the order of comp differs, and
+    // nothing below depends on it (every choice is by (degree, index)).
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
     auto bfs_levels = [&](int32_t s, std::vector<int32_t>& comp, int& depth) {
         comp.clear();
         comp.push_back(s);
         level[s] = 0;
         depth = 0;
-        for (size_t h = 0; h < comp.size(); ++h) {
-            int32_t v = comp[h];
-            for (int32_t w : adj[(size_t)v])
-                if (level[w] < 0) {
-                    level[w] = level[v] + 1;
-                    depth = std::max(depth, level[w]);
-                    comp.push_back(w);
+        size_t fb = 0, fe = 1;
+        std::vector<std::vector<int32_t>> part;
+        while (fb < fe) {
+            const int32_t next = depth + 1;
+            const int64_t F = (int64_t)(fe - fb);
+            const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw, F / 512));
+            part.assign((size_t)nt, {});
+            auto expand = [&](int64_t t) {
+                std::vector<int32_t>& out = part[(size_t)t];
+                for (size_t h = fb + (size_t)(F * t / nt); h < fb + (size_t)(F * (t + 1) / nt); ++h) {
+                    const int32_t v = comp[h];
+                    for (const int32_t* pw = adj_begin(v); pw != adj_end(v); ++pw) {
+                        int32_t* lw = &level[(size_t)*pw];
+                        int32_t expect = -1;
+                        if (__atomic_load_n(lw, __ATOMIC_RELAXED) < 0 &&
+                            __atomic_compare_exchange_n(lw, &expect, next, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED))
+                            out.push_back(*pw);
+                    }
                 }
+            };
+            std::vector<std::thread> pool;
+            for (int64_t t = 1; t < nt; ++t) pool.emplace_back(expand, t);
+            expand(0);
+            for (auto& th : pool) th.join();
+            fb = fe;
+            for (const auto& p : part) comp.insert(comp.end(), p.begin(), p.end());
+            fe = comp.size();
+            if (fe > fb) depth = next;
         }
     };
     std::vector<int32_t> comp;
@@ -199,10 +267,10 @@ extern "C" rbffd_status rbffd_rcm_order_host(const int64_t* rowptr, const int32_
         for (size_t h = 0; h < queue.size(); ++h) {
             int32_t v = queue[h];
             order.push_back(v);
-            for (int32_t w : adj[(size_t)v])
-                if (!done[(size_t)w]) {
-                    done[(size_t)w] = 1;
-                    queue.push_back(w);
+            for (const int32_t* pw = adj_begin(v); pw != adj_end(v); ++pw)
+                if (!done[(size_t)*pw]) {
+                    done[(size_t)*pw] = 1;
+                    queue.push_back(*pw);
                 }
         }
     }
