@@ -67,3 +67,80 @@ def test_components_and_invalid(R):
     with pytest.raises(R.RbffdError) as exc:
         R.rcm_order_host(np.array([0, 1]), np.array([5]))    # column out of range
     assert exc.value.status == 1
+
+
+def _rcm_reference(S):
+    """The same reverse Cuthill-McKee, written plainly and sequentially:
+    George-Liu pseudo-peripheral start (from the component's node of least
+    (degree, index), up to 8 moves to the least-(degree, index) node of the
+    deepest BFS level while the depth grows), then a BFS visiting neighbours
+    by (degree, index), components in order of their first node, reversed."""
+    n = S.shape[0]
+    S = S.tolil()
+    S.setdiag(0)
+    S = S.tocsr()
+    S.eliminate_zeros()
+    deg = np.diff(S.indptr)
+    adj = [sorted(S.indices[S.indptr[i]:S.indptr[i + 1]].tolist(), key=lambda j: (deg[j], j)) for i in range(n)]
+
+    def levels(s):
+        lev = {s: 0}
+        q = [s]
+        for v in q:
+            for w in adj[v]:
+                if w not in lev:
+                    lev[w] = lev[v] + 1
+                    q.append(w)
+        return lev
+
+    done = np.zeros(n, bool)
+    order = []
+    for seed in range(n):
+        if done[seed]:
+            continue
+        comp = levels(seed)
+        start = min(comp, key=lambda v: (deg[v], v))
+        d0 = -1
+        for _ in range(8):
+            lev = levels(start)
+            depth = max(lev.values())
+            best = min((v for v, l in lev.items() if l == depth), key=lambda v: (deg[v], v))
+            if depth <= d0:
+                break
+            d0 = depth
+            if best == start:
+                break
+            start = best
+        q = [start]
+        done[start] = True
+        for v in q:
+            order.append(v)
+            for w in adj[v]:
+                if not done[w]:
+                    done[w] = True
+                    q.append(w)
+    return np.array(order[::-1], dtype=np.int32)
+
+
+def test_large_graph_matches_sequential_definition(R):
+    """70,000-node graph (a 200 x 160 grid with diagonals; a 30,000-node
+    random graph of degree ~8, whose BFS levels grow to thousands of nodes;
+    more small components, isolated nodes; asymmetric and repeated edges;
+    shuffled): large enough for the threaded adjacency build and the threaded
+    level-synchronous BFS, whose permutation must equal the plain sequential
+    one exactly."""
+    rng = np.random.default_rng(9)
+    w, h = 200, 160
+    idx = np.arange(w * h).reshape(h, w)
+    e = [np.stack([idx[:, :-1].ravel(), idx[:, 1:].ravel()], 1),
+         np.stack([idx[:-1, :].ravel(), idx[1:, :].ravel()], 1),
+         np.stack([idx[:-1, :-1].ravel(), idx[1:, 1:].ravel()], 1)]
+    g0 = w * h
+    expander = g0 + np.stack([np.repeat(np.arange(30000), 4), rng.integers(0, 30000, 120000)], 1)
+    extra = g0 + 30000 + rng.integers(0, 6000, (9000, 2))      # small components among the next 6000 nodes
+    n = g0 + 30000 + 8000                                        # the last 2000 nodes are isolated
+    e = np.concatenate(e + [expander, extra, e[0][:500]])        # repeats
+    A = _shuffle(_csr(n, e), 3)                                  # asymmetric: each edge stored once
+    perm = R.rcm_order_host(A.indptr, A.indices)
+    assert sorted(perm.tolist()) == list(range(n))
+    assert np.array_equal(perm, _rcm_reference(A + A.T))
