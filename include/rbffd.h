@@ -1,8 +1,8 @@
 /*
  * rbffd.h - C ABI of the GB300 (sm_103a) RBF-FD surface Laplace-Beltrami
  * library: batched per-stencil operator build with a per-stencil shape
- * parameter, fixed-width (sliced ELL) application, and IMEX (SBDF2 +
- * BiCGSTAB) reaction-diffusion stepping.
+ * parameter, fixed-width (sliced ELL) application, and IMEX (SBDF of order
+ * 1-4 + BiCGSTAB) reaction-diffusion stepping.
  *
  * Method: Shankar, Wright, Kirby, Fogelson, "A Radial Basis Function
  * (RBF)-Finite Difference (FD) Method for Diffusion and Reaction-Diffusion
@@ -14,7 +14,9 @@
  *    device; "host" pointers are ordinary host memory.  Arrays are dense and
  *    C-contiguous.  Node coordinates and normals are N x 3 row-major float64.
  *  - The caller owns every buffer it passes; the library owns what it
- *    allocates inside an rbffd_op / rbffd_mlp until the matching destroy.
+ *    allocates inside an rbffd_op / rbffd_mlp until the matching destroy,
+ *    and the transient scratch of its calls, which lives in a library-owned
+ *    memory pool (rbffd_memory_pool_config, rbffd_release_memory).
  *  - Work is queued on the given stream (a cudaStream_t passed as void*;
  *    NULL is the legacy default stream).  Calls that return data to host
  *    memory or a status depending on device results synchronise that stream.
