@@ -25,7 +25,9 @@ Schnakenberg and Gray-Scott kinetics of the synthetic workloads.
 
 Pins: tests/test_oracle_stepping.py (BiCGSTAB against a dense solve; SBDF2
 with L = -lambda I against its closed-form recurrence; constant steady states
-stay constant; heat-equation decay of Y_3^2 on the sphere).
+stay constant; heat-equation decay of Y_3^2 on the sphere; every monomial of
+each kinetics recovered exactly by interpolation on a grid; Gray-Scott's
+double-root equilibrium (1/2, 1/5) and its Jacobians).
 """
 from __future__ import annotations
 

@@ -190,3 +190,81 @@ def test_implicit_source_keeps_order(order):
         assert out["t"] == pytest.approx(T)
         errs.append(abs(out["u"][0] - exact(T)))
     assert abs(math.log2(errs[0] / errs[1]) - order) < 0.3
+
+
+def _monomials(fn, deg=3):
+    """Coefficients c[a, b] of u^a v^b (a, b <= deg) of the polynomial fn(u, v),
+    recovered exactly (to rounding) by interpolation on a (deg+1)^2 grid: a
+    polynomial of that bidegree is determined by its values there."""
+    pts = np.arange(deg + 1, dtype=np.float64) - 1.0      # -1, 0, 1, 2
+    U, V = np.meshgrid(pts, pts, indexing="ij")
+    Vd = np.polynomial.polynomial.polyvander2d(U.ravel(), V.ravel(), [deg, deg])
+    return np.linalg.solve(Vd, fn(U.ravel(), V.ravel())).reshape(deg + 1, deg + 1)
+
+
+def _expect(terms, deg=3):
+    c = np.zeros((deg + 1, deg + 1))
+    for (a, b), val in terms.items():
+        c[a, b] = val
+    return c
+
+
+def test_barrio_kinetics_every_term():
+    """Eqs. turing1/turing2 with Table tur_param's constants: every monomial of
+    f = alpha u - alpha tau1 u v^2 + v - tau2 u v and of
+    g = beta v + alpha tau1 u v^2 + gamma u + tau2 u v has the coefficient the
+    equations give, and no other monomial appears (a dropped term, a wrong
+    sign or u^2 v for u v^2 changes one of them)."""
+    for row in GOLDEN["turing_table"]["rows"]:
+        p = dict(model="barrio", **{k: row[k] for k in ("alpha", "beta", "gamma", "tau1", "tau2")})
+        a, b, g, t1, t2 = p["alpha"], p["beta"], p["gamma"], p["tau1"], p["tau2"]
+        cf = _monomials(lambda u, v: ostp.reaction(p, u, v)[0])
+        cg = _monomials(lambda u, v: ostp.reaction(p, u, v)[1])
+        np.testing.assert_allclose(cf, _expect({(1, 0): a, (1, 2): -a * t1, (0, 1): 1.0, (1, 1): -t2}),
+                                   atol=1e-12)
+        np.testing.assert_allclose(cg, _expect({(0, 1): b, (1, 2): a * t1, (1, 0): g, (1, 1): t2}),
+                                   atol=1e-12)
+        # the mixed derivatives at the origin that the terms above fix
+        assert cf[1, 1] == pytest.approx(-t2, abs=1e-12) and 2 * cf[1, 2] == pytest.approx(-2 * a * t1)
+        assert cg[1, 1] == pytest.approx(t2, abs=1e-12) and 2 * cg[1, 2] == pytest.approx(2 * a * t1)
+
+
+def test_gray_scott_kinetics_every_term_and_double_root():
+    """Gray-Scott f = -u v^2 + F (1 - u), g = u v^2 - (F + k) v: every monomial,
+    the Jacobian diag(-F, -(F + k)) at the trivial state (1, 0), and for
+    F = 0.04, k = 0.06 -- where F^2 = 4 F (F + k)^2, so the two nontrivial
+    equilibria merge -- the double root (u, v) = (1/2, 1/5) with f = g = 0
+    there and a singular Jacobian (a saddle-node)."""
+    p = W.GRAY_SCOTT
+    F, k = p["F"], p["k"]
+    cf = _monomials(lambda u, v: ostp.reaction(p, u, v)[0])
+    cg = _monomials(lambda u, v: ostp.reaction(p, u, v)[1])
+    np.testing.assert_allclose(cf, _expect({(0, 0): F, (1, 0): -F, (1, 2): -1.0}), atol=1e-13)
+    np.testing.assert_allclose(cg, _expect({(1, 2): 1.0, (0, 1): -(F + k)}), atol=1e-13)
+    assert F * F == pytest.approx(4 * F * (F + k) ** 2, rel=1e-12)
+    us, vs = (F + k) / (F / (2 * (F + k))), F / (2 * (F + k))
+    assert (us, vs) == (pytest.approx(0.5), pytest.approx(0.2))
+    f, g = ostp.reaction(p, np.array([us]), np.array([vs]))
+    assert abs(f[0]) < 1e-16 and abs(g[0]) < 1e-16
+
+    def jac(u0, v0, h=1e-6):
+        fu = (np.array(ostp.reaction(p, np.array([u0 + h]), np.array([v0])))
+              - np.array(ostp.reaction(p, np.array([u0 - h]), np.array([v0])))) / (2 * h)
+        fv = (np.array(ostp.reaction(p, np.array([u0]), np.array([v0 + h])))
+              - np.array(ostp.reaction(p, np.array([u0]), np.array([v0 - h])))) / (2 * h)
+        return np.array([[fu[0, 0], fv[0, 0]], [fu[1, 0], fv[1, 0]]])
+
+    np.testing.assert_allclose(jac(1.0, 0.0), [[-F, 0.0], [0.0, -(F + k)]], atol=1e-9)
+    J = jac(us, vs)
+    np.testing.assert_allclose(J, [[-vs * vs - F, -2 * us * vs], [vs * vs, 2 * us * vs - (F + k)]], atol=1e-9)
+    assert abs(np.linalg.det(J)) < 1e-9
+
+
+def test_schnakenberg_kinetics_every_term():
+    """Schnakenberg f = gamma (a - u + u^2 v), g = gamma (b - u^2 v)."""
+    p = W.SCHNAKENBERG
+    a, b, g = p["a"], p["b"], p["gamma"]
+    cf = _monomials(lambda u, v: ostp.reaction(p, u, v)[0])
+    cg = _monomials(lambda u, v: ostp.reaction(p, u, v)[1])
+    np.testing.assert_allclose(cf, _expect({(0, 0): g * a, (1, 0): -g, (2, 1): g}), atol=1e-13)
+    np.testing.assert_allclose(cg, _expect({(0, 0): g * b, (2, 1): -g}), atol=1e-13)
