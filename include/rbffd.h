@@ -330,8 +330,10 @@ void rbffd_destroy(rbffd_op* op);
  * Returns RBFFD_ESINGULAR when some rows had an out-of-range index or a
  * local matrix that is not numerically positive definite (those rows are
  * NaN).  Synchronises the stream.  The first call on a device looks up the
- * array's device address (once per device, with that device current); make
- * that first call before any stream capture.  All calls share the one array
+ * array's device address (once per device, with that device current, kept
+ * for the life of the process: after a cudaDeviceReset of that device the
+ * kept address is stale and this call must not be used again); make that
+ * first call before any stream capture.  All calls share the one array
  * and its failure counter, which keep the last call's contents: the counter
  * is cleared at the start of each call, and calls whose work overlaps on the
  * GPU (different streams or threads without ordering) race on the array.

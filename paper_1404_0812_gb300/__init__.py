@@ -134,7 +134,9 @@ def stencil_weights_noalloc(nodes, normals, stencils, eps, kernel="imq", weights
     """rbffd_stencil_weights_noalloc: weights (rows x n float64) of caller-given
     stencils (rows x n int32, centre first) at caller-given eps, computed
     without any device allocation inside the library.  ``weights`` may be a
-    preallocated CUDA float64 tensor."""
+    preallocated CUDA float64 tensor.  Shapes are checked before anything
+    reaches the library (the C call trusts N = nodes.shape[0], rows and n)."""
+    _check_noalloc_shapes(nodes, normals, stencils, eps, weights)
     lib = _lib.load()
     nodes = _dev(nodes, torch.float64)
     normals = _dev(normals, torch.float64)
@@ -144,11 +146,34 @@ def stencil_weights_noalloc(nodes, normals, stencils, eps, kernel="imq", weights
     if weights is None:
         weights = torch.empty((rows, n), dtype=torch.float64, device=stencils.device)
     _dev(weights, torch.float64)
+    here = torch.device("cuda", torch.cuda.current_device())
+    for name, t in (("nodes", nodes), ("normals", normals), ("stencils", stencils), ("eps", eps),
+                    ("weights", weights)):
+        if t.device != here:
+            raise ValueError(f"{name} is on {t.device}, not on the current device {here}")
     _lib.check(lib.rbffd_stencil_weights_noalloc(_ptr(nodes), _ptr(normals), nodes.shape[0], _ptr(stencils),
                                                  rows, n, _ptr(eps), KERNELS[kernel] if isinstance(kernel, str)
                                                  else int(kernel), _ptr(weights), _stream(stream)),
                "rbffd_stencil_weights_noalloc")
     return weights
+
+
+def _check_noalloc_shapes(nodes, normals, stencils, eps, weights=None):
+    """Shapes of rbffd_stencil_weights_noalloc's arguments: nodes and normals
+    N x 3, stencils rows x n, eps (rows,), weights (rows, n) when given.
+    Raises ValueError otherwise (a short array would be read or written past
+    its end on the device)."""
+    if nodes.dim() != 2 or nodes.shape[1] != 3:
+        raise ValueError(f"nodes must be N x 3, got shape {tuple(nodes.shape)}")
+    if tuple(normals.shape) != tuple(nodes.shape):
+        raise ValueError(f"normals shape {tuple(normals.shape)} != nodes shape {tuple(nodes.shape)}")
+    if stencils.dim() != 2:
+        raise ValueError(f"stencils must be rows x n, got shape {tuple(stencils.shape)}")
+    rows, n = stencils.shape
+    if tuple(eps.shape) != (rows,):
+        raise ValueError(f"eps shape {tuple(eps.shape)} != ({rows},)")
+    if weights is not None and tuple(weights.shape) != (rows, n):
+        raise ValueError(f"weights shape {tuple(weights.shape)} != ({rows}, {n})")
 
 
 def apply(op: Operator, u, y=None, stream=None):

@@ -1399,14 +1399,13 @@ weights_rows_kernel(const double* __restrict__ X, const double* __restrict__ NR,
     Lane S{scratch + warp_global * 32 * (int64_t)lane_size + lane_id};
     const int npad = (n + 3) / 4 * 4;
     const Layout ly = make_layout(npad, true);
-    const int m = ly.m, XS = ly.XS;
+    const int m = ly.m;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += stride) {
         double* w_row = Wout + r * (int64_t)n;
         Geo geo;
         bool ok = load_geometry_row(S, ly, n, stencils + r * (int64_t)n, X, NR, N, geo);
         double eps_s = ok ? eps[r] * geo.rs : 0.0;
-        double e2 = eps_s * eps_s;
         double s = 0.0;
         if (ok) {
             assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH);
@@ -1423,43 +1422,9 @@ weights_rows_kernel(const double* __restrict__ X, const double* __restrict__ NR,
             for (int j = 0; j < n; ++j) w_row[j] = NAN;
             continue;
         }
-        double n0x = S[ly.NS], n0y = S[ly.NS + m], n0z = S[ly.NS + 2 * m];
-        for (int d = 0; d < 3; ++d)
-            for (int i = 0; i < m; ++i) S[ly.GV + d * m + i] = 0.0;
-        for (int j = 1; j < n; ++j) {
-            double ps = psi_from_phi(kernel, e2, S[ly.PH + pk(j, 0)]);
-            double dx = -S[XS + j], dy = -S[XS + m + j], dz = -S[XS + 2 * m + j];
-            double nd = n0x * dx + n0y * dy + n0z * dz;
-            S[ly.GV + j] = ps * (dx - n0x * nd);
-            S[ly.GV + m + j] = ps * (dy - n0y * nd);
-            S[ly.GV + 2 * m + j] = ps * (dz - n0z * nd);
-        }
-        for (int d = 0; d < 3; ++d) aug_solve0(S, ly, n, ly.GV + d * m, s);
-        for (int i = 0; i < n; ++i) {
-            double gx = S[ly.GV + i], gy = S[ly.GV + m + i], gz = S[ly.GV + 2 * m + i];
-            double nx = S[ly.NS + i], ny = S[ly.NS + m + i], nz = S[ly.NS + 2 * m + i];
-            double nd = nx * gx + ny * gy + nz * gz;
-            S[ly.HV + i] = gx - nx * nd;
-            S[ly.HV + m + i] = gy - ny * nd;
-            S[ly.HV + 2 * m + i] = gz - nz * nd;
-        }
+        // the build's own weight arithmetic (same steps, same order)
+        first_row_weights(S, ly, n, kernel, eps_s, s);
         const int V = ly.Q0;
-        for (int i = 0; i < m; ++i) S[V + i] = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double xi = S[XS + i], yi = S[XS + m + i], zi = S[XS + 2 * m + i];
-            double hx = S[ly.HV + i], hy = S[ly.HV + m + i], hz = S[ly.HV + 2 * m + i];
-            double vi = 0.0;
-            int base = pk(i, 0);
-            for (int j = 0; j < i; ++j) {
-                double ps = psi_from_phi(kernel, e2, S[ly.PH + base + j]);
-                double dx = xi - S[XS + j], dy = yi - S[XS + m + j], dz = zi - S[XS + 2 * m + j];
-                double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
-                S[V + j] = fma(ps, dx * hx + dy * hy + dz * hz, S[V + j]);
-                vi = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi);
-            }
-            S[V + i] += vi;
-        }
-        aug_solve0(S, ly, n, V, s);
         double inv_rs2 = 1.0 / (geo.rs * geo.rs);
         for (int j = 0; j < n; ++j) w_row[j] = S[V + j] * inv_rs2;
     }

@@ -47,3 +47,29 @@ def test_argument_checks_need_no_gpu():
     assert lib.rbffd_fp64_mma_peak(None, None) == _lib.EINVAL
     assert lib.rbffd_build_operator(None, None, 10, None, 5, None, None, None) == _lib.EINVAL
     assert b"NULL" in lib.rbffd_last_error() or b"invalid" in lib.rbffd_last_error()
+
+
+def test_noalloc_binding_rejects_mismatched_shapes_before_the_call():
+    """stencil_weights_noalloc checks every shape before anything reaches the
+    library, whose kernel trusts N = nodes.shape[0], rows and n (a short
+    array would be read or written past its end on the device).  CPU
+    tensors: the shape check fires first, no GPU is touched."""
+    import torch
+    import paper_1404_0812_gb300 as R
+    f64, i32 = torch.float64, torch.int32
+    X, Nr = torch.zeros(50, 3, dtype=f64), torch.zeros(50, 3, dtype=f64)
+    S, e, w = torch.zeros(8, 10, dtype=i32), torch.zeros(8, dtype=f64), torch.zeros(8, 10, dtype=f64)
+    bad = [
+        dict(nodes=torch.zeros(50, 2, dtype=f64)),        # not N x 3
+        dict(nodes=torch.zeros(150, dtype=f64)),          # flat
+        dict(normals=torch.zeros(49, 3, dtype=f64)),      # fewer normals than nodes
+        dict(stencils=torch.zeros(80, dtype=i32)),        # not rows x n
+        dict(eps=torch.zeros(7, dtype=f64)),              # shorter than rows
+        dict(weights=torch.zeros(8, 9, dtype=f64)),       # smaller than rows x n
+        dict(weights=torch.zeros(7, 10, dtype=f64)),
+    ]
+    for b in bad:
+        kw = dict(nodes=X, normals=Nr, stencils=S, eps=e, weights=w)
+        kw.update(b)
+        with pytest.raises(ValueError, match="shape|must be"):
+            R.stencil_weights_noalloc(**kw)

@@ -4,10 +4,11 @@ of the apply, through the C ABI, against the CPU oracle.
 Tolerances (floating point; derived from the arithmetic):
 * applied operator, smooth u: ||L_gpu u - L_cpu u||_inf / ||L_cpu u||_inf
   <= 1e-8 (also at kappa_T = 1e12);
-* applied operator, random u at kappa_T = 1e12: <= 5e-5 -- two exact-in-
-  exact-arithmetic float64 orderings of the same weights already differ by
-  3.5e-6 there (kappa_T * unit roundoff amplification), so the bound is 15x
-  that spread; at kappa <= 1e8 random u is held to 1e-8;
+* applied operator, random u at kappa_T = 1e12: the float64 oracle is itself
+  ~1.2e-6 (relative L-infinity) from the 45-digit truth there, so GPU against
+  oracle is held to 5e-6 (the two errors, each at most ~2x that spread); the
+  arbitration by the 45-digit oracle is in test_gpu_parity_hp.py and in the
+  full-size test below; at kappa <= 1e8 random u is held to 1e-8;
 * stencil indices: bit-exact (the (d^2, index) key is bit-reproducible);
 * eps: |eps_gpu - eps_cpu| <= 2 * tol + 1e-5 * eps (both searches stop
   within tol of the root; the root itself moves with kappa's float64 noise).
@@ -18,6 +19,7 @@ import numpy as np
 import pytest
 import torch
 
+import hp_arbiter as H
 from oracle import operator as oop
 from oracle import stencils as ost
 from oracle import weights as ow
@@ -64,7 +66,10 @@ def test_weights_at_oracle_eps(R, sphere):
     y_s = R.apply(op, T(u_s)).cpu().numpy()
     y_r = R.apply(op, T(u_r)).cpu().numpy()
     assert rel_inf(y_s, oop.apply(ref, u_s)) <= 1e-8
-    assert rel_inf(y_r, oop.apply(ref, u_r)) <= 5e-5
+    # random u at kappa_T = 1e12: the float64 oracle is itself ~1e-6 from the
+    # 45-digit weights (test_gpu_parity_hp); GPU and oracle differ by their two
+    # errors, held to three times the oracle's measured spread there
+    assert rel_inf(y_r, oop.apply(ref, u_r)) <= 5e-6
     # float32 apply of the float32 weights against the float64 oracle
     y32 = R.apply(op, T(u_s, torch.float32)).cpu().numpy().astype(np.float64)
     assert rel_inf(y32, oop.apply(ref, u_s)) <= 1e-3
@@ -164,18 +169,24 @@ def test_full_size_mixed_build_sampled(R):
     assert np.all(np.abs(np.log(info["kappa"] / 1e12)) < 0.05)
     idx, w = R.get_rows(op)
     rng = np.random.default_rng(0)
-    rows = np.concatenate([rng.choice(np.where(nper == n)[0], 6, replace=False) for n in (31, 50, 70, 101)])
+    rows = np.concatenate([rng.choice(np.where(nper == n)[0], 3, replace=False) for n in (31, 50, 70, 101)])
     rows = np.concatenate([rows, [0, ns.N - 1]])
     idx_r = idx[torch.as_tensor(rows, device="cuda")].cpu().numpy()
     w_r = w[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    st, wg = [], []
     for r, k in enumerate(rows):
         n = int(nper[k])
         sref = ost.stencil(ns.X, int(k), n)
         assert np.array_equal(idx_r[r, :n], sref.astype(np.int32))
-        wref = ow.stencil_weights(ns.X[sref], ns.normals[sref], info["eps"][k], ow.IMQ)
-        assert np.abs(w_r[r, :n] - wref).max() <= 5e-4 * np.abs(wref).max()
-        u = W.sph_harm_y32(ns.X[sref])
-        assert abs(w_r[r, :n] @ u - wref @ u) <= 1e-8 * np.abs(wref).sum() * np.abs(u).max()
+        st.append(sref)
+        wg.append(w_r[r, :n])
+    # weights and applied rows (relative L-infinity over the sampled rows)
+    # against the 45-digit oracle, no worse than the float64 oracle's
+    res = H.arbitrate(ns.X, ns.normals, rows, st, info["eps"][rows], ow.IMQ, wg,
+                      {"y32": W.sph_harm_y32(ns.X), "random": W.uniform_field(ns.N, seed=1)})
+    print(res)
+    H.assert_no_worse_than_f64(res)
+    assert res["y32"]["gpu"] <= 1e-8
     for k in rows[::4]:
         n = int(nper[k])
         sref = ost.stencil(ns.X, int(k), n)

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+import hp_arbiter as H
 from oracle import stencils as ost
 from oracle import weights as ow
 from paper_1404_0812_gb300 import workloads as W
@@ -60,6 +61,7 @@ def test_learned_full_size_sampled_rows(R, built):
     rows = np.concatenate([rows, [0, ns.N - 1]])
     sel = torch.as_tensor(rows, device="cuda")
     idx_r, w_r = idx[sel].cpu().numpy(), w[sel].cpu().numpy()
+    st, wg = [], []
     for r, k in enumerate(rows):
         n = int(nper[k])
         sref = ost.stencil(ns.X, int(k), n)
@@ -69,10 +71,17 @@ def test_learned_full_size_sampled_rows(R, built):
         if info["status"][k] == 4:    # accepted prediction: inside the band by the oracle's kappa
             assert 0.5e12 * 0.999 <= kc <= 2e12 * 1.001
         assert abs(np.log(kc / info["kappa"][k])) < 1e-3
-        wref = ow.stencil_weights(P, ns.normals[sref], info["eps"][k], ow.IMQ)
-        assert np.abs(w_r[r, :n] - wref).max() <= 5e-4 * np.abs(wref).max()
-        # the applied operator at this row against the oracle's weights
-        assert abs(y[k] - wref @ u[sref]) <= 1e-8 * np.abs(wref).sum() * np.abs(u).max()
+        # the apply reproduces the stored weights' row exactly (same float64 sum)
+        assert abs(y[k] - w_r[r, :n] @ u[sref]) <= 1e-12 * np.abs(w_r[r, :n]).sum() * np.abs(u).max()
+        st.append(sref)
+        wg.append(w_r[r, :n])
+    # weights and applied rows (relative L-infinity over the sampled rows)
+    # against the 45-digit oracle: no worse than the float64 oracle's
+    res = H.arbitrate(ns.X, ns.normals, rows, st, info["eps"][rows], ow.IMQ, wg,
+                      {"y32": u, "random": W.uniform_field(ns.N, seed=1)})
+    print(res)
+    H.assert_no_worse_than_f64(res)
+    assert res["y32"]["gpu"] <= 1e-8
 
 
 @pytest.mark.parametrize("dtype,tol,bound", [(torch.float64, 1e-10, 1e-9), (torch.float32, 1e-6, 2e-5)])
@@ -118,14 +127,19 @@ def test_pointcloud_2m_build_sampled_rows(R, nets):
     rows = np.random.default_rng(2).choice(ns.N, 8, replace=False)
     sel = torch.as_tensor(rows, device="cuda")
     idx_r, w_r = idx[sel].cpu().numpy(), w[sel].cpu().numpy()
+    st, wg = [], []
     for r, k in enumerate(rows):
         sref = ost.stencil(ns.X, int(k), n)
         assert np.array_equal(idx_r[r, :n], sref.astype(np.int32))
         P = ns.X[sref]
         kc = ow.cond2(ow.interp_matrix(P, info["eps"][k], ow.IMQ))
         assert abs(np.log(kc / info["kappa"][k])) < 1e-3
-        wref = ow.stencil_weights(P, ns.normals[sref], info["eps"][k], ow.IMQ)
-        assert np.abs(w_r[r, :n] - wref).max() <= 5e-4 * np.abs(wref).max()
+        st.append(sref)
+        wg.append(w_r[r, :n])
+    res = H.arbitrate(ns.X, ns.normals, rows, st, info["eps"][rows], ow.IMQ, wg,
+                      {"random": W.uniform_field(ns.N, seed=1)})
+    print(res)
+    H.assert_no_worse_than_f64(res)
 
 
 def test_torus_40k_schnakenberg_float32_against_float64_oracle(R):

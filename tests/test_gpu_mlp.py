@@ -104,3 +104,72 @@ def test_mlp_load_replaces_parameters(R):
     assert torch.equal(a.predict(x), b.predict(x))
     with pytest.raises(ValueError):
         a.load(p2[:-1])
+
+
+def _unpack_like(W, flat, p):
+    return W.mlp_unpack(np.asarray(flat, dtype=np.float64), p["W1"].shape[0])
+
+
+
+def test_adam_update_matches_oracle_exactly_given_the_gradient(R):
+    """rbffd_mlp_train's optimiser step against oracle.mlp.adam_step (float64)
+    at t = 1 and t = 2 (first and second moments, both bias corrections).
+    Every sample is the same, so the shuffled full batch (epochs = 1, batch =
+    count) sums exactly the tiles rbffd_mlp_loss_grad sums: the GPU gradient
+    at each step is known bit for bit, and the oracle's Adam applied to it
+    must give the GPU's new parameters up to float32 rounding."""
+    n, B = 31, 256
+    D = 3 * n
+    p64 = W.mlp_init(D, seed=21)
+    p32 = W.mlp_pack(p64).astype(np.float32)
+    net = R.EpsNet(n, p32)
+    rng = np.random.default_rng(22)
+    x = np.repeat(rng.uniform(-1, 1, (1, D)), B, axis=0).astype(np.float32)
+    t = np.full(B, -0.7, dtype=np.float32)
+    X, Tt = T(x, torch.float32), T(t, torch.float32)
+    ref = {k: v.astype(np.float32).astype(np.float64) for k, v in p64.items()}
+    state = {}
+    for step in (1, 2):
+        g, _ = net.loss_grad(X, Tt)                      # gradient at the GPU's current params
+        g = _unpack_like(W, g.cpu().numpy(), p64)
+        net.train(X, Tt, epochs=1, batch=B, lr=1e-3, seed=step)
+        om.adam_step(ref, g, state, lr=1e-3)
+        got, want = net.params().astype(np.float64), W.mlp_pack(ref)
+        err = np.abs(got - want)
+        assert err.max() <= 1e-7 * max(1.0, np.abs(want).max()), (step, err.max())
+        # the GPU continues from its own float32 parameters
+        ref = {k: v.astype(np.float32).astype(np.float64) for k, v in
+               W.mlp_unpack(got, D).items()}
+
+
+def test_adam_full_batch_steps_match_float64_oracle(R):
+    """Two full-batch rbffd_mlp_train steps (distinct samples) from known
+    parameters against oracle.mlp.loss_and_grads + adam_step in float64.
+    Parameters whose gradient is at least 1e-2 of the largest (the float32
+    gradient is within 1e-4 of the largest, test above, so their direction
+    is fixed) must move as the oracle moves them, to 2e-2 of the learning
+    rate; the rest by at most the learning rate times Adam's bound."""
+    n, B = 50, 512
+    D = 3 * n
+    p64 = W.mlp_init(D, seed=31)
+    net = R.EpsNet(n, W.mlp_pack(p64).astype(np.float32))
+    rng = np.random.default_rng(32)
+    x = rng.uniform(-1, 1, (B, D)).astype(np.float32)
+    t = rng.normal(-1.0, 0.3, B).astype(np.float32)
+    X, Tt = T(x, torch.float32), T(t, torch.float32)
+    ref = {k: v.astype(np.float32).astype(np.float64) for k, v in p64.items()}
+    state = {}
+    lr = 1e-3
+    prev = W.mlp_pack(ref)
+    for step in (1, 2):
+        _, g = om.loss_and_grads(ref, x.astype(np.float64), t.astype(np.float64))
+        om.adam_step(ref, g, state, lr=lr)
+        net.train(X, Tt, epochs=1, batch=B, lr=lr, seed=step)
+        got, want = net.params().astype(np.float64), W.mlp_pack(ref)
+        gf = np.abs(W.mlp_pack(g))
+        well = gf >= 1e-2 * gf.max()
+        assert well.sum() > 100
+        assert np.abs(got - want)[well].max() <= 2e-2 * lr, step
+        # a bias-corrected Adam step moves a coordinate by at most ~lr at
+        # t = 1 and 2 (Cauchy-Schwarz on m_hat / sqrt(v_hat): <= 1.0014 lr)
+        assert np.abs(got - prev).max() <= 1.01 * lr * step
