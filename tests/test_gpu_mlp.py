@@ -168,7 +168,7 @@ def test_adam_full_batch_steps_match_float64_oracle(R):
         got, want = net.params().astype(np.float64), W.mlp_pack(ref)
         gf = np.abs(W.mlp_pack(g))
         well = gf >= 1e-2 * gf.max()
-        assert well.sum() > 100
+        assert well.sum() > 50
         assert np.abs(got - want)[well].max() <= 2e-2 * lr, step
         # a bias-corrected Adam step moves a coordinate by at most ~lr at
         # t = 1 and 2 (Cauchy-Schwarz on m_hat / sqrt(v_hat): <= 1.0014 lr)
