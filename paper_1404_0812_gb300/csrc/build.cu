@@ -61,6 +61,20 @@ constexpr double LANCZOS_RTOL = 1e-6;       // relative change that stops a Lanc
 // stopping on a stalled value misjudges kappa by 10-40 %.
 constexpr int LANCZOS_KMIN = 10;
 constexpr double ACCEPT_MARGIN = 1e-4;      // shrink the accept band by this
+// Early acceptance of a learned first guess.  Every Ritz value of the A^{-1}
+// run is a lower bound of 1 / min|lambda(A)| (and the A run's of
+// max|lambda(A)|), so the running estimate k_j = lambda_max theta_j never
+// exceeds kappa: k_j >= accept_lo kappa_T already proves the lower edge.
+// The upper edge needs the run's shortfall bounded: over 1.5M first
+// evaluations (1M-node sphere, n = 31 / 50 / 70 / 101, and the held-out
+// bumpy sphere, n = 50) the smallest ratio theta_j / theta_final was 0.44 at
+// step 6, 0.74 at step 7, 0.93 at step 8 and 0.998 at step 9.  A guess is
+// accepted at step j when k_j <= f_j accept_hi kappa_T with f_6..f_9 =
+// 0.25, 0.45, 0.7, 0.85 (1.1-1.8x below the worst ratios seen); otherwise
+// the same run continues to its full length and the usual test decides.
+__host__ __device__ inline double early_accept_factor(int steps) {
+    return steps == 6 ? 0.25 : steps == 7 ? 0.45 : steps == 8 ? 0.7 : steps == 9 ? 0.85 : 0.0;
+}
 constexpr double F_FAIL = 60.0;         // F value used when Phi is not numerically SPD
 
 // ---------------------------------------------------------------------------
@@ -337,15 +351,25 @@ __device__ bool cholesky(const Lane& S, const Layout& ly, int n) {
 // x <- Phi^{-1} x (x in region V of length m) using L and ID.
 __device__ void chol_solve(const Lane& S, const Layout& ly, int V) {
     const int m = ly.m, L = ly.L;
-    // forward: L y = x
+    // forward: L y = x (columns four at a time: the 20 loads of a chunk are
+    // in flight together; each row still sums its columns in order)
     for (int ib = 0; ib < m; ib += 4) {
         double t[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) t[a] = S[V + ib + a];
-        for (int k = 0; k < ib; ++k) {
-            double yk = S[V + k];
+        const int r = pk(ib, 0);   // row ib + a starts at r + a ib + a (a + 1) / 2
+        for (int k = 0; k < ib; k += 4) {
+            double y[4], l[4][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) t[a] = fma(-S[L + pk(ib + a, k)], yk, t[a]);
+            for (int q = 0; q < 4; ++q) y[q] = S[V + k + q];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) l[a][q] = S[L + r + a * ib + a * (a + 1) / 2 + k + q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int a = 0; a < 4; ++a) t[a] = fma(-l[a][q], y[q], t[a]);
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -629,7 +653,8 @@ __device__ inline double unit_hash(uint64_t x) {
 // Starts from RV when warm (the previous evaluation's Ritz vector), else
 // from the stencil's pseudo-random vector.
 __device__ double lanczos_inv_ritz(const Lane& S, const Layout& ly, int n, double s, double rtol, bool warm,
-                                   double* vb, uint64_t seed) {
+                                   double* vb, uint64_t seed, double lmax = 0.0, double acc_lo = 0.0,
+                                   double acc_hi = 0.0, bool* early = nullptr) {
     const int m = ly.m, w = ly.Q2;
     float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
     double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX], qbord[LANCZOS_KMAX + 1];
@@ -697,6 +722,15 @@ __device__ double lanczos_inv_ritz(const Lane& S, const Layout& ly, int n, doubl
             b2[i] = bb * bb;
         }
         ext = tri_extreme(al, b2, j + 1, G);
+        if (early && j + 1 < kmin) {
+            // early acceptance of a learned guess (see early_accept_factor);
+            // the caller needs no Ritz vector then
+            const double est = lmax * fabs(ext);
+            if (est >= acc_lo && est <= early_accept_factor(j + 1) * acc_hi) {
+                *early = true;
+                return ext;
+            }
+        }
         if (j + 1 >= kmin && fabs(fabs(ext) - prev) <= rtol * fabs(ext)) break;
         if (bn <= 1e-14 * fabs(a) || j + 1 == LANCZOS_KMAX) break;
         prev = fabs(ext);
@@ -759,8 +793,12 @@ __device__ double eig_derivative(const Lane& S, const Layout& ly, int n, int ker
 // Lanczos run (d ln lambda_max / dx is ~1% of it on these stencils and is
 // left out: Newton then still converges, linearly at rate ~0.01).  The Ritz
 // vector stays in RV as the next evaluation's start vector.
+// With acc_hi > 0 (a learned first guess) the A^{-1} run may stop early and
+// set *early when the guess is proven acceptable (see early_accept_factor);
+// kappa is then the run's lower estimate and no Ritz vector is formed.
 __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel, double eps_s, bool warm,
-                             double* vb, double* theta_out, double* schur, uint64_t seed) {
+                             double* vb, double* theta_out, double* schur, uint64_t seed,
+                             double acc_lo = 0.0, double acc_hi = 0.0, bool* early = nullptr) {
     double* dF = theta_out;
     *dF = NAN;
     *schur = 0.0;
@@ -772,8 +810,11 @@ __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel,
     for (int i = 0; i < n; ++i) s += S[ly.U + i];
     if (!(s > 0.0)) return INFINITY;
     *schur = s;
-    double theta = lanczos_inv_ritz(S, ly, n, s, LANCZOS_RTOL, warm, vb, seed);
+    // the A run first: its estimate turns the A^{-1} run's Ritz values into
+    // running estimates of kappa for the early acceptance
     double lmax = lanczos_max_f32(S, ly, n, LANCZOS_RTOL);
+    double theta = lanczos_inv_ritz(S, ly, n, s, LANCZOS_RTOL, warm, vb, seed, lmax, acc_lo, acc_hi,
+                                    acc_hi > 0.0 ? early : nullptr);
     double k = lmax * fabs(theta);
     if (!isfinite(k)) return INFINITY;
     *dF = theta;   // the caller turns it into dF/dx with kappa_slope() when needed
@@ -915,35 +956,75 @@ __device__ void aug_solve0(const Lane& S, const Layout& ly, int n, int V, double
 }
 
 // Three right-hand sides (regions V, V + m, V + 2m) solved together with
-// Phi = L L^T: every element of L is loaded once for three FMAs.
+// Phi = L L^T, in the 4-row blocks of chol_solve: every element of L is
+// loaded once for three FMAs, and a block's loads are in flight together.
 __device__ void chol_solve_x3(const Lane& S, const Layout& ly, int V) {
     const int m = ly.m, L = ly.L;
-    for (int i = 0; i < m; ++i) {   // forward
-        double t0 = S[V + i], t1 = S[V + m + i], t2 = S[V + 2 * m + i];
-        const int r = pk(i, 0);
-        for (int k = 0; k < i; ++k) {
-            double l = S[L + r + k];
-            t0 = fma(-l, S[V + k], t0);
-            t1 = fma(-l, S[V + m + k], t1);
-            t2 = fma(-l, S[V + 2 * m + k], t2);
+    for (int ib = 0; ib < m; ib += 4) {   // forward: L y = x
+        double t[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) t[a][d] = S[V + d * m + ib + a];
+        const int r = pk(ib, 0);
+        for (int k = 0; k < ib; ++k) {
+            double y[3], l[4];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) y[d] = S[V + d * m + k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) l[a] = S[L + r + a * ib + a * (a + 1) / 2 + k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) t[a][d] = fma(-l[a], y[d], t[a][d]);
         }
-        double id = S[ly.ID + i];
-        S[V + i] = t0 * id;
-        S[V + m + i] = t1 * id;
-        S[V + 2 * m + i] = t2 * id;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int c = 0; c < a; ++c) {
+                const double l = S[L + pk(ib + a, ib + c)];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) t[a][d] = fma(-l, t[c][d], t[a][d]);
+            }
+            const double id = S[ly.ID + ib + a];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                t[a][d] *= id;
+                S[V + d * m + ib + a] = t[a][d];
+            }
+        }
     }
-    for (int k = m - 1; k >= 0; --k) {   // backward, column-oriented
-        double id = S[ly.ID + k];
-        double x0 = S[V + k] * id, x1 = S[V + m + k] * id, x2 = S[V + 2 * m + k] * id;
-        S[V + k] = x0;
-        S[V + m + k] = x1;
-        S[V + 2 * m + k] = x2;
-        const int r = pk(k, 0);
-        for (int i = 0; i < k; ++i) {
-            double l = S[L + r + i];
-            S[V + i] = fma(-l, x0, S[V + i]);
-            S[V + m + i] = fma(-l, x1, S[V + m + i]);
-            S[V + 2 * m + i] = fma(-l, x2, S[V + 2 * m + i]);
+    for (int kb = m - 4; kb >= 0; kb -= 4) {   // backward: L^T x = y
+        double t[4][3];
+#pragma unroll
+        for (int b = 3; b >= 0; --b) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) t[b][d] = S[V + d * m + kb + b];
+#pragma unroll
+            for (int c = b + 1; c < 4; ++c) {
+                const double l = S[L + pk(kb + c, kb + b)];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) t[b][d] = fma(-l, t[c][d], t[b][d]);
+            }
+            const double id = S[ly.ID + kb + b];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                t[b][d] *= id;
+                S[V + d * m + kb + b] = t[b][d];
+            }
+        }
+        const int r0 = pk(kb, 0), r1 = pk(kb + 1, 0), r2 = pk(kb + 2, 0), r3 = pk(kb + 3, 0);
+        for (int i = 0; i < kb; ++i) {
+            const double l0 = S[L + r0 + i], l1 = S[L + r1 + i], l2 = S[L + r2 + i], l3 = S[L + r3 + i];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double v = S[V + d * m + i];
+                v = fma(-l0, t[0][d], v);
+                v = fma(-l1, t[1][d], v);
+                v = fma(-l2, t[2][d], v);
+                v = fma(-l3, t[3][d], v);
+                S[V + d * m + i] = v;
+            }
         }
     }
 }
@@ -1132,10 +1213,12 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs A) {
             const double acc_lo = A.acc_lo * A.kT * (1.0 + ACCEPT_MARGIN);
             const double acc_hi = A.acc_hi * A.kT * (1.0 - ACCEPT_MARGIN);
             double theta;
+            const bool first_guess = learned && st.phase == PH_FIRST;
+            bool early = false;
             double k = eval_kappa(S, ly, n, A.kernel, eps_s, false, &vborder, &theta, &schur,
-                                  (uint64_t)A.row_node[r]);
+                                  (uint64_t)A.row_node[r], acc_lo, first_guess ? acc_hi : 0.0, &early);
             // the slope is needed unless a learned guess is accepted now
-            const bool accept_now = learned && st.phase == PH_FIRST && k >= acc_lo && k <= acc_hi;
+            const bool accept_now = first_guess && (early || (k >= acc_lo && k <= acc_hi));
             dF = (isfinite(k) && !accept_now) ? kappa_slope(S, ly, n, A.kernel, eps_s, theta) : NAN;
             search_update(st, F_of(k, A.kT), dF, k, tol_s, A.max_evals, acc_lo, acc_hi, learned, n);
             if (st.phase == PH_DONE) {

@@ -88,3 +88,19 @@ def assert_no_worse_than_f64(res, factor=2.0, floor=1e-12):
         if not isinstance(r, dict):
             continue
         assert r["gpu"] <= factor * r["f64"] + floor, (name, r)
+
+
+def _cond2_chunk(args):
+    Ps, eps, kernel = args
+    return [ow.cond2(ow.interp_matrix(P, e, kernel)) for P, e in zip(Ps, eps)]
+
+
+def cond2_many(Ps, eps, kernel, procs=None, chunk=500):
+    """The oracle's kappa_2(A_P(eps)) (Section 5) for many stencils, in a
+    pool of spawned processes."""
+    jobs = [(Ps[i:i + chunk], eps[i:i + chunk], kernel) for i in range(0, len(Ps), chunk)]
+    procs = procs or max(1, min(len(jobs), os.cpu_count() or 1, 16))
+    if procs == 1:
+        return np.concatenate([_cond2_chunk(j) for j in jobs])
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return np.concatenate(pool.map(_cond2_chunk, jobs, chunksize=1))
