@@ -151,6 +151,14 @@ __device__ __forceinline__ double phi_of(int kernel, double e2r2) {
 __device__ __forceinline__ double psi_from_phi(int kernel, double e2, double ph) {
     return kernel == RBFFD_GAUSSIAN ? -2.0 * e2 * ph : -e2 * ph * ph * ph;
 }
+// psi = psi_scale * psi_shape(phi): the pair pass of the weights sums
+// psi_shape terms and applies the constant factor once per entry
+__device__ __forceinline__ double psi_shape(int kernel, double ph) {
+    return kernel == RBFFD_GAUSSIAN ? ph : ph * ph * ph;
+}
+__device__ __forceinline__ double psi_scale(int kernel, double e2) {
+    return kernel == RBFFD_GAUSSIAN ? -2.0 * e2 : -e2;
+}
 
 // ---------------------------------------------------------------------------
 // stencil geometry: centre-translated, r_s-scaled coordinates and normals
@@ -348,68 +356,106 @@ __device__ bool cholesky(const Lane& S, const Layout& ly, int n) {
     return true;
 }
 
-// x <- Phi^{-1} x (x in region V of length m) using L and ID.
-__device__ void chol_solve(const Lane& S, const Layout& ly, int V) {
+// x_d <- Phi^{-1} x_d for NR right-hand sides (regions V[d], length m) using
+// L and ID: forward L y = x, then backward L^T x = y, in blocks of four rows.
+// A chunk of C = 4 / NR columns (forward) or rows (backward) is loaded before
+// its FMAs issue, so each step keeps 4 C + NR C loads in flight for 4 C NR
+// FMAs; every row still sums its columns in increasing order (forward) and
+// receives the blocks' updates from the last block down (backward), whatever
+// NR is, so a right-hand side gets the same bits alone or with others.
+template <int NR>
+__device__ void chol_solve_multi(const Lane& S, const Layout& ly, const int (&V)[NR]) {
+    constexpr int C = NR == 1 ? 4 : NR == 2 ? 2 : 1;
     const int m = ly.m, L = ly.L;
-    // forward: L y = x (columns four at a time: the 20 loads of a chunk are
-    // in flight together; each row still sums its columns in order)
-    for (int ib = 0; ib < m; ib += 4) {
-        double t[4];
+    for (int ib = 0; ib < m; ib += 4) {   // forward
+        double t[4][NR];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) t[a] = S[V + ib + a];
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int d = 0; d < NR; ++d) t[a][d] = S[V[d] + ib + a];
         const int r = pk(ib, 0);   // row ib + a starts at r + a ib + a (a + 1) / 2
-        for (int k = 0; k < ib; k += 4) {
-            double y[4], l[4][4];
+        for (int k = 0; k < ib; k += C) {   // ib is a multiple of 4, hence of C
+            double y[C][NR], l[4][C];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) y[q] = S[V + k + q];
+            for (int q = 0; q < C; ++q)
+#pragma unroll
+                for (int d = 0; d < NR; ++d) y[q][d] = S[V[d] + k + q];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) l[a][q] = S[L + r + a * ib + a * (a + 1) / 2 + k + q];
+                for (int q = 0; q < C; ++q) l[a][q] = S[L + r + a * ib + a * (a + 1) / 2 + k + q];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < C; ++q)
 #pragma unroll
-                for (int a = 0; a < 4; ++a) t[a] = fma(-l[a][q], y[q], t[a]);
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int d = 0; d < NR; ++d) t[a][d] = fma(-l[a][q], y[q][d], t[a][d]);
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
 #pragma unroll
-            for (int c = 0; c < a; ++c) t[a] = fma(-S[L + pk(ib + a, ib + c)], t[c], t[a]);
-            t[a] *= S[ly.ID + ib + a];
-            S[V + ib + a] = t[a];
+            for (int c = 0; c < a; ++c) {
+                const double l = S[L + pk(ib + a, ib + c)];
+#pragma unroll
+                for (int d = 0; d < NR; ++d) t[a][d] = fma(-l, t[c][d], t[a][d]);
+            }
+            const double id = S[ly.ID + ib + a];
+#pragma unroll
+            for (int d = 0; d < NR; ++d) {
+                t[a][d] *= id;
+                S[V[d] + ib + a] = t[a][d];
+            }
         }
     }
-    // backward: L^T x = y
-    for (int kb = m - 4; kb >= 0; kb -= 4) {
-        double t[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) t[b] = S[V + kb + b];
+    for (int kb = m - 4; kb >= 0; kb -= 4) {   // backward
+        double t[4][NR];
 #pragma unroll
         for (int b = 3; b >= 0; --b) {
 #pragma unroll
-            for (int c = b + 1; c < 4; ++c) t[b] = fma(-S[L + pk(kb + c, kb + b)], t[c], t[b]);
-            t[b] *= S[ly.ID + kb + b];
-            S[V + kb + b] = t[b];
+            for (int d = 0; d < NR; ++d) t[b][d] = S[V[d] + kb + b];
+#pragma unroll
+            for (int c = b + 1; c < 4; ++c) {
+                const double l = S[L + pk(kb + c, kb + b)];
+#pragma unroll
+                for (int d = 0; d < NR; ++d) t[b][d] = fma(-l, t[c][d], t[b][d]);
+            }
+            const double id = S[ly.ID + kb + b];
+#pragma unroll
+            for (int d = 0; d < NR; ++d) {
+                t[b][d] *= id;
+                S[V[d] + kb + b] = t[b][d];
+            }
         }
         const int r0 = pk(kb, 0), r1 = pk(kb + 1, 0), r2 = pk(kb + 2, 0), r3 = pk(kb + 3, 0);
-        // kb is a multiple of 4: four rows per pass keep four independent
-        // FMA chains in flight
-        for (int i = 0; i < kb; i += 4) {
-            double v[4];
+        for (int i = 0; i < kb; i += C) {
+            double l[4][C], v[C][NR];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = S[V + i + q];
+            for (int q = 0; q < C; ++q) {
+                l[0][q] = S[L + r0 + i + q];
+                l[1][q] = S[L + r1 + i + q];
+                l[2][q] = S[L + r2 + i + q];
+                l[3][q] = S[L + r3 + i + q];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r0 + i + q], t[0], v[q]);
+                for (int d = 0; d < NR; ++d) v[q][d] = S[V[d] + i + q];
+            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r1 + i + q], t[1], v[q]);
+            for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r2 + i + q], t[2], v[q]);
+                for (int q = 0; q < C; ++q)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = fma(-S[L + r3 + i + q], t[3], v[q]);
+                    for (int d = 0; d < NR; ++d) v[q][d] = fma(-l[b][q], t[b][d], v[q][d]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) S[V + i + q] = v[q];
+            for (int q = 0; q < C; ++q)
+#pragma unroll
+                for (int d = 0; d < NR; ++d) S[V[d] + i + q] = v[q][d];
         }
     }
+}
+
+// x <- Phi^{-1} x (x in region V of length m)
+__device__ void chol_solve(const Lane& S, const Layout& ly, int V) {
+    const int R[1] = {V};
+    chol_solve_multi<1>(S, ly, R);
 }
 
 // ---------------------------------------------------------------------------
@@ -647,17 +693,13 @@ __device__ inline double unit_hash(uint64_t x) {
     return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// Lanczos with A^{-1} keeping its basis (regions QB + j m, borders in
-// qbord[]): returns the signed Ritz value theta of largest magnitude and
-// writes the unit Ritz vector (m entries, border in *vb) to region RV.
-// Starts from RV when warm (the previous evaluation's Ritz vector), else
-// from the stencil's pseudo-random vector.
-__device__ double lanczos_inv_ritz(const Lane& S, const Layout& ly, int n, double s, double rtol, bool warm,
-                                   double* vb, uint64_t seed, double lmax = 0.0, double acc_lo = 0.0,
-                                   double acc_hi = 0.0, bool* early = nullptr) {
-    const int m = ly.m, w = ly.Q2;
-    float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
-    double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX], qbord[LANCZOS_KMAX + 1];
+// Start vector of the A^{-1} Lanczos run, normalised, in region QB (m
+// entries) with its border entry returned: the previous evaluation's Ritz
+// vector (region RV, border *vb) when warm, else the stencil's
+// pseudo-random vector.
+__device__ double lanczos_inv_start(const Lane& S, const Layout& ly, int n, bool warm, const double* vb,
+                                    uint64_t seed) {
+    const int m = ly.m;
     double nrm2 = 0.0;
     for (int i = 0; i < m; ++i) {
         double v = i < n ? (warm ? S[ly.RV + i] : unit_hash(seed * 131u + i)) : 0.0;
@@ -668,15 +710,31 @@ __device__ double lanczos_inv_ritz(const Lane& S, const Layout& ly, int n, doubl
     nrm2 += qb * qb;
     double inrm = rsqrt(nrm2);
     for (int i = 0; i < n; ++i) S[ly.QB + i] *= inrm;
-    qbord[0] = qb * inrm;
+    return qb * inrm;
+}
+
+// Lanczos with A^{-1} keeping its basis (regions QB + j m, borders in
+// qbord[]) from the start vector in QB (border qb0; with w0_ready its first
+// Phi^{-1} product is already in region Q2): returns the signed Ritz value
+// theta of largest magnitude and writes the unit Ritz vector (m entries,
+// border in *vb) to region RV.
+__device__ double lanczos_inv_ritz(const Lane& S, const Layout& ly, int n, double s, double rtol, bool warm,
+                                   double qb0, bool w0_ready, double* vb, double lmax = 0.0,
+                                   double acc_lo = 0.0, double acc_hi = 0.0, bool* early = nullptr) {
+    const int m = ly.m, w = ly.Q2;
+    float al[LANCZOS_KMAX], b2[LANCZOS_KMAX];
+    double alpha_d[LANCZOS_KMAX], beta_d[LANCZOS_KMAX], qbord[LANCZOS_KMAX + 1];
+    qbord[0] = qb0;
     const int kmin = warm ? 2 : LANCZOS_KMIN;
     double beta = 0.0, prev = -1.0, ext = 0.0;
     int k = 0;
     for (int j = 0; j < LANCZOS_KMAX; ++j) {
         const int qj = ly.QB + j * m, qp = ly.QB + (j - 1) * m;
         // [c; d] = A^{-1} [f; g]: c0 = Phi^{-1} f, d = (1^T c0 - g) / s, c = c0 - d u
-        for (int i = 0; i < m; ++i) S[w + i] = S[qj + i];
-        chol_solve(S, ly, w);
+        if (j > 0 || !w0_ready) {
+            for (int i = 0; i < m; ++i) S[w + i] = S[qj + i];
+            chol_solve(S, ly, w);
+        }
         double sp[4] = {0.0, 0.0, 0.0, 0.0};
         for (int i = 0; i < m; i += 4)
 #pragma unroll
@@ -804,8 +862,17 @@ __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel,
     *schur = 0.0;
     assemble_phi(S, ly, n, kernel, eps_s, ly.L, ly.PH, ly.PF);
     if (!cholesky(S, ly, n)) return INFINITY;
-    for (int i = 0; i < ly.m; ++i) S[ly.U + i] = i < n ? 1.0 : 0.0;
-    chol_solve(S, ly, ly.U);
+    // u = Phi^{-1} 1 and the A^{-1} run's first product Phi^{-1} q_0 in one
+    // pass over L
+    const double qb0 = lanczos_inv_start(S, ly, n, warm, vb, seed);
+    for (int i = 0; i < ly.m; ++i) {
+        S[ly.U + i] = i < n ? 1.0 : 0.0;
+        S[ly.Q2 + i] = S[ly.QB + i];
+    }
+    {
+        const int R[2] = {ly.U, ly.Q2};
+        chol_solve_multi<2>(S, ly, R);
+    }
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += S[ly.U + i];
     if (!(s > 0.0)) return INFINITY;
@@ -813,7 +880,7 @@ __device__ double eval_kappa(const Lane& S, const Layout& ly, int n, int kernel,
     // the A run first: its estimate turns the A^{-1} run's Ritz values into
     // running estimates of kappa for the early acceptance
     double lmax = lanczos_max_f32(S, ly, n, LANCZOS_RTOL);
-    double theta = lanczos_inv_ritz(S, ly, n, s, LANCZOS_RTOL, warm, vb, seed, lmax, acc_lo, acc_hi,
+    double theta = lanczos_inv_ritz(S, ly, n, s, LANCZOS_RTOL, warm, qb0, true, vb, lmax, acc_lo, acc_hi,
                                     acc_hi > 0.0 ? early : nullptr);
     double k = lmax * fabs(theta);
     if (!isfinite(k)) return INFINITY;
@@ -848,6 +915,17 @@ __device__ inline double clampd(double v, double lo, double hi) { return fmin(fm
 // dF/dx near the root, about -(11 + n / 10) on quasi-uniform surface
 // stencils (measured); used when the computed derivative is unusable.
 __device__ inline double slope_model(int n) { return -(11.0 + 0.1 * n); }
+
+// A learned guess predicts the root (kappa = kappa_T).  The search starts a
+// slope model's step past it, at kappa ~0.85 kappa_T: early acceptance (see
+// early_accept_factor) needs the estimate well below the band's upper edge,
+// and the networks' errors leave more room below kappa_T than above it
+// inside [0.5, 2] kappa_T.  On the 1M-node sphere this aim moves more first
+// evaluations into the step-7 window than it pushes out of the band.
+constexpr double LEARNED_AIM = 0.85;
+__device__ inline double learned_start(float guess, int n) {
+    return (double)guess + log(LEARNED_AIM) / slope_model(n);
+}
 
 __device__ inline void finish(Search& s, double x, double k, int status) {
     s.x_ret = x;
@@ -955,78 +1033,11 @@ __device__ void aug_solve0(const Lane& S, const Layout& ly, int n, int V, double
     for (int i = 0; i < n; ++i) S[V + i] = fma(-d, S[ly.U + i], S[V + i]);
 }
 
-// Three right-hand sides (regions V, V + m, V + 2m) solved together with
-// Phi = L L^T, in the 4-row blocks of chol_solve: every element of L is
-// loaded once for three FMAs, and a block's loads are in flight together.
+// Three right-hand sides (regions V, V + m, V + 2m) solved together: every
+// element of L is loaded once for three FMAs.
 __device__ void chol_solve_x3(const Lane& S, const Layout& ly, int V) {
-    const int m = ly.m, L = ly.L;
-    for (int ib = 0; ib < m; ib += 4) {   // forward: L y = x
-        double t[4][3];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) t[a][d] = S[V + d * m + ib + a];
-        const int r = pk(ib, 0);
-        for (int k = 0; k < ib; ++k) {
-            double y[3], l[4];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) y[d] = S[V + d * m + k];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) l[a] = S[L + r + a * ib + a * (a + 1) / 2 + k];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) t[a][d] = fma(-l[a], y[d], t[a][d]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-#pragma unroll
-            for (int c = 0; c < a; ++c) {
-                const double l = S[L + pk(ib + a, ib + c)];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) t[a][d] = fma(-l, t[c][d], t[a][d]);
-            }
-            const double id = S[ly.ID + ib + a];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                t[a][d] *= id;
-                S[V + d * m + ib + a] = t[a][d];
-            }
-        }
-    }
-    for (int kb = m - 4; kb >= 0; kb -= 4) {   // backward: L^T x = y
-        double t[4][3];
-#pragma unroll
-        for (int b = 3; b >= 0; --b) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) t[b][d] = S[V + d * m + kb + b];
-#pragma unroll
-            for (int c = b + 1; c < 4; ++c) {
-                const double l = S[L + pk(kb + c, kb + b)];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) t[b][d] = fma(-l, t[c][d], t[b][d]);
-            }
-            const double id = S[ly.ID + kb + b];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                t[b][d] *= id;
-                S[V + d * m + kb + b] = t[b][d];
-            }
-        }
-        const int r0 = pk(kb, 0), r1 = pk(kb + 1, 0), r2 = pk(kb + 2, 0), r3 = pk(kb + 3, 0);
-        for (int i = 0; i < kb; ++i) {
-            const double l0 = S[L + r0 + i], l1 = S[L + r1 + i], l2 = S[L + r2 + i], l3 = S[L + r3 + i];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                double v = S[V + d * m + i];
-                v = fma(-l0, t[0][d], v);
-                v = fma(-l1, t[1][d], v);
-                v = fma(-l2, t[2][d], v);
-                v = fma(-l3, t[3][d], v);
-                S[V + d * m + i] = v;
-            }
-        }
-    }
+    const int R[3] = {V, V + ly.m, V + 2 * ly.m};
+    chol_solve_multi<3>(S, ly, R);
 }
 
 __device__ void aug_solve0_x3(const Lane& S, const Layout& ly, int n, int V, double s) {
@@ -1073,7 +1084,8 @@ __device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int ke
     }
     const int V = ly.Q0;
     for (int i = 0; i < m; ++i) S[V + i] = 0.0;
-    // pair (i, j), j < i: v_j += psi (x_i - x_j) . h_i ; v_i += psi (x_j - x_i) . h_j.
+    // pair (i, j), j < i: v_j += psi (x_i - x_j) . h_i ; v_i += psi (x_j - x_i) . h_j,
+    // summed with psi_shape and scaled by psi_scale at the end.
     // Rows in blocks of four: x_j, h_j and v_j are loaded once per column for
     // the four rows (a third of the scratch accesses of one row at a time).
     // Every v_j still receives the rows' contributions in row order and every
@@ -1098,7 +1110,7 @@ __device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int ke
             double vj = S[V + j];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const double ps = psi_from_phi(kernel, e2, S[ly.PH + r0 + a * i + a * (a + 1) / 2 + j]);
+                const double ps = psi_shape(kernel, S[ly.PH + r0 + a * i + a * (a + 1) / 2 + j]);
                 const double dx = xi[a] - xj, dy = yi[a] - yj, dz = zi[a] - zj;
                 vj = fma(ps, dx * hx[a] + dy * hy[a] + dz * hz[a], vj);
                 vi[a] = fma(-ps, dx * hjx + dy * hjy + dz * hjz, vi[a]);
@@ -1111,7 +1123,7 @@ __device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int ke
 #pragma unroll
             for (int c = 0; c < a; ++c) {
                 const int j = i + c;
-                const double ps = psi_from_phi(kernel, e2, S[ly.PH + pk(i + a, j)]);
+                const double ps = psi_shape(kernel, S[ly.PH + pk(i + a, j)]);
                 const double dx = xi[a] - S[XS + j], dy = yi[a] - S[XS + m + j], dz = zi[a] - S[XS + 2 * m + j];
                 const double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
                 S[V + j] = fma(ps, dx * hx[a] + dy * hy[a] + dz * hz[a], S[V + j]);
@@ -1126,7 +1138,7 @@ __device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int ke
         double vi = 0.0;
         int base = pk(i, 0);
         for (int j = 0; j < i; ++j) {
-            double ps = psi_from_phi(kernel, e2, S[ly.PH + base + j]);
+            double ps = psi_shape(kernel, S[ly.PH + base + j]);
             double dx = xi - S[XS + j], dy = yi - S[XS + m + j], dz = zi - S[XS + 2 * m + j];
             double hjx = S[ly.HV + j], hjy = S[ly.HV + m + j], hjz = S[ly.HV + 2 * m + j];
             S[V + j] = fma(ps, dx * hx + dy * hy + dz * hz, S[V + j]);
@@ -1134,6 +1146,8 @@ __device__ void first_row_weights(const Lane& S, const Layout& ly, int n, int ke
         }
         S[V + i] += vi;
     }
+    const double cs = psi_scale(kernel, e2);
+    for (int j = 0; j < n; ++j) S[V + j] *= cs;
     aug_solve0(S, ly, n, V, s);
 }
 
@@ -1195,7 +1209,7 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs A) {
                 st.uhi = A.xhi;
                 float gs = A.guess_rows ? A.guess_rows[r] : NAN;
                 learned = isfinite(gs);
-                st.x_next = clampd(learned ? (double)gs : log(1.0 / geo.mean_d), A.xlo, A.xhi);
+                st.x_next = clampd(learned ? learned_start(gs, n) : log(1.0 / geo.mean_d), A.xlo, A.xhi);
             }
         }
         if (__ballot_sync(0xffffffffu, have) == 0) {
@@ -2051,7 +2065,7 @@ __global__ void __launch_bounds__(64) search_dd_kernel(SearchDDArgs D) {
                 const double tol_s = A.tol * geo.rs;
                 const float gs = A.guess_rows ? A.guess_rows[r] : NAN;
                 const bool learned = isfinite(gs);
-                st.x_next = clampd(learned ? (double)gs : log(1.0 / geo.mean_d), A.xlo, A.xhi);
+                st.x_next = clampd(learned ? learned_start(gs, n) : log(1.0 / geo.mean_d), A.xlo, A.xhi);
                 const double acc_lo = A.acc_lo * A.kT * (1.0 + ACCEPT_MARGIN);
                 const double acc_hi = A.acc_hi * A.kT * (1.0 - ACCEPT_MARGIN);
                 while (st.phase != PH_DONE) {
