@@ -175,7 +175,15 @@ typedef struct {
     const void* source_v;   /*   s(t, x) = exp(source_rate t) h(x) added to the */
     double source_rate;     /*   species' equation and taken at t^{n+1}, i.e.   */
                             /*   implicitly (Section 6's forced diffusion tests) */
+    int solver;         /* RBFFD_SOLVER_BICGSTAB (0, Section 4.2 / Section 6) or
+                           RBFFD_SOLVER_BANDED_LU (Section 7: each implicit
+                           matrix factorised once, two substitutions per
+                           step; see rbffd_lu_factor -- the nodes should be in
+                           a bandwidth-reducing order).  tol / maxit apply to
+                           BiCGSTAB only; an LU step reports 0 iterations */
 } rbffd_step_params;
+
+enum { RBFFD_SOLVER_BICGSTAB = 0, RBFFD_SOLVER_BANDED_LU = 1 };
 
 /*
  * State of an IMEX run.  All vectors are caller-owned device arrays of N
@@ -227,6 +235,41 @@ typedef struct {
  */
 rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* state, const rbffd_step_params* params,
                              int64_t nsteps, void* stream, rbffd_step_report* report);
+
+/* ------------------------------------------------------------------------
+ * Direct solves (Section 7 factors the SBDF2 matrix once by a sparse LU and
+ * uses the triangular factors for a forward and a back substitution every
+ * step).  M = alpha I - beta L_X in node order is factorised as a banded
+ * matrix with partial pivoting (row interchanges; LAPACK's banded-LU
+ * layout): lower / upper bandwidths kl / ku of L_X (rbffd_op_bandwidth), U
+ * with upper bandwidth kl + ku.  Bandwidths come from the node numbering:
+ * renumber by reverse Cuthill-McKee first (rbffd_rcm_order, Section 4.1);
+ * the factor takes (2 kl + ku + 1) N + (kl + 1) N values of the dtype.
+ * ---------------------------------------------------------------------- */
+typedef struct rbffd_lu rbffd_lu;     /* opaque, library-owned factor */
+
+/* Largest i - j (*kl) and j - i (*ku) over the nonzeros (i, j) of op's
+ * matrix in node order.  Synchronises the stream. */
+rbffd_status rbffd_op_bandwidth(const rbffd_op* op, int64_t* kl, int64_t* ku, void* stream);
+
+/*
+ * rbffd_lu_factor - factorise M = alpha I - beta L_X (for SBDF2 alpha = 3,
+ * beta = 2 dt delta) in dtype (RBFFD_F32 with op's float32 weights,
+ * RBFFD_F64 with its float64 weights).  Synchronises the stream.  Returns
+ * RBFFD_ESINGULAR when a pivot column is exactly zero, RBFFD_EINVAL when
+ * kl + ku is too large for the substitutions' shared-memory window (about
+ * 3,200 in float64 / 6,400 in float32 at full prefetch depth, twice that at
+ * half depth), RBFFD_ENOMEM when the band does not fit, RBFFD_TIMEOUT when a
+ * bounded grid barrier gave up.  *out is NULL on failure.
+ */
+rbffd_status rbffd_lu_factor(const rbffd_op* op, double alpha, double beta, int dtype, void* stream,
+                             rbffd_lu** out);
+/* x = M^{-1} b (device vectors of N values of the factor's dtype, node
+ * order; x may alias b).  Asynchronous on the stream. */
+rbffd_status rbffd_lu_solve(const rbffd_lu* lu, const void* b, void* x, void* stream);
+/* Device bytes held by the factor. */
+int64_t rbffd_lu_bytes(const rbffd_lu* lu);
+void rbffd_lu_destroy(rbffd_lu* lu);
 
 /*
  * Per-stencil results of the build, in node order (device outputs, each

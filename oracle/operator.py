@@ -91,3 +91,12 @@ def dense(op: Operator, N: int) -> np.ndarray:
     for r in range(op.R):
         np.add.at(L[op.rows[r]], op.idx[r, :op.n[r]], op.w[r, :op.n[r]])
     return L
+
+
+def sparse_matrix(op: Operator, N: int):
+    """L_X as a scipy CSR matrix (N x N, Section 4: n_k entries in row k)."""
+    import scipy.sparse as sps
+    rows = np.repeat(op.rows, op.n)
+    cols = np.concatenate([op.idx[r, :op.n[r]] for r in range(op.R)])
+    vals = np.concatenate([op.w[r, :op.n[r]] for r in range(op.R)])
+    return sps.csr_matrix((vals, (rows, cols)), shape=(N, N))

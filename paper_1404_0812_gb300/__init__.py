@@ -314,6 +314,7 @@ class StepParams:
     source_u: torch.Tensor | None = None   # forcing exp(source_rate t) h(x), taken at t^{n+1}
     source_v: torch.Tensor | None = None
     source_rate: float = 0.0
+    solver: str = "bicgstab"   # or "lu": banded LU factors, two substitutions per step
 
 
 @dataclass
@@ -380,6 +381,7 @@ def step_imex(op: Operator, state: StepState, params: StepParams, nsteps: int, s
         if h is not None:
             setattr(sp, name, _dev(h, params.dtype).data_ptr())
     sp.source_rate = float(params.source_rate)
+    sp.solver = {"bicgstab": _lib.SOLVER_BICGSTAB, "lu": _lib.SOLVER_BANDED_LU}[params.solver]
     cs = _lib.State(_ptr(state.u), _ptr(state.v), _ptr(state.u_prev), _ptr(state.v_prev),
                     _ptr(state.f_prev), _ptr(state.g_prev), state.has_history, state.step,
                     _ptr(state.u_prev2), _ptr(state.v_prev2), _ptr(state.f_prev2), _ptr(state.g_prev2),
@@ -395,6 +397,61 @@ def step_imex(op: Operator, state: StepState, params: StepParams, nsteps: int, s
                 max_iters_v=rep.max_iters_v, total_iters=rep.total_iters,
                 last_relres_u=rep.last_relres_u, last_relres_v=rep.last_relres_v,
                 failed_step=rep.failed_step)
+
+
+# ---------------------------------------------------------------------------
+# direct solves (banded LU)
+# ---------------------------------------------------------------------------
+
+def op_bandwidth(op: Operator, stream=None):
+    """rbffd_op_bandwidth -> (kl, ku) of op's matrix in node order."""
+    kl, ku = C.c_int64(), C.c_int64()
+    _lib.check(_lib.load().rbffd_op_bandwidth(op.handle, C.byref(kl), C.byref(ku), _stream(stream)),
+               "rbffd_op_bandwidth")
+    return kl.value, ku.value
+
+
+class LU:
+    """Handle of a library-owned banded LU factor (rbffd_lu) of
+    alpha I - beta L_X."""
+
+    def __init__(self, handle, N, dtype):
+        self.handle = handle
+        self.N = N
+        self.dtype = dtype
+
+    @property
+    def bytes(self) -> int:
+        return int(_lib.load().rbffd_lu_bytes(self.handle))
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.load().rbffd_lu_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def lu_factor(op: Operator, alpha: float, beta: float, dtype=torch.float64, stream=None) -> LU:
+    """rbffd_lu_factor: banded LU (partial pivoting) of alpha I - beta L_X."""
+    h = C.c_void_p()
+    _lib.check(_lib.load().rbffd_lu_factor(op.handle, float(alpha), float(beta),
+                                           F32 if dtype == torch.float32 else F64, _stream(stream), C.byref(h)),
+               "rbffd_lu_factor")
+    return LU(h, op.N, dtype)
+
+
+def lu_solve(lu: LU, b, x=None, stream=None):
+    """rbffd_lu_solve: x = (alpha I - beta L_X)^{-1} b (x may be b)."""
+    b = _dev(b, lu.dtype)
+    if b.shape != (lu.N,):
+        raise ValueError(f"b must have shape ({lu.N},)")
+    if x is None:
+        x = torch.empty_like(b)
+    _dev(x, lu.dtype)
+    _lib.check(_lib.load().rbffd_lu_solve(lu.handle, _ptr(b), _ptr(x), _stream(stream)), "rbffd_lu_solve")
+    return x
 
 
 def fp64_peak(stream=None) -> float:

@@ -18,6 +18,7 @@ GAUSSIAN, IMQ = 0, 1
 F32, F64 = 0, 1
 PREC_F64, PREC_DD = 0, 1
 MODEL_NONE, MODEL_LINEAR, MODEL_SCHNAKENBERG, MODEL_GRAY_SCOTT, MODEL_BARRIO = range(5)
+SOLVER_BICGSTAB, SOLVER_BANDED_LU = 0, 1
 STENCIL_OK, STENCIL_NO_BRACKET, STENCIL_NO_CONVERGENCE, STENCIL_SINGULAR, STENCIL_ACCEPTED_PREDICTION = range(5)
 
 vp = C.c_void_p
@@ -44,7 +45,7 @@ class StepParams(C.Structure):
     _fields_ = [("model", C.c_int), ("nspecies", C.c_int), ("dtype", C.c_int), ("dt", C.c_double),
                 ("delta_u", C.c_double), ("delta_v", C.c_double), ("coef", C.c_double * 8),
                 ("tol", C.c_double), ("maxit", C.c_int), ("use_graph", C.c_int), ("order", C.c_int),
-                ("source_u", vp), ("source_v", vp), ("source_rate", C.c_double)]
+                ("source_u", vp), ("source_v", vp), ("source_rate", C.c_double), ("solver", C.c_int)]
 
 
 class State(C.Structure):
@@ -95,6 +96,11 @@ SIGNATURES = {
     "rbffd_selftest_barrier_timeout": (C.c_int, [vp]),
     "rbffd_stencil_weights_noalloc": (C.c_int, [vp, vp, C.c_int64, vp, C.c_int64, C.c_int, vp, C.c_int,
                                                 vp, vp]),
+    "rbffd_op_bandwidth": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]),
+    "rbffd_lu_factor": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, vp, C.POINTER(vp)]),
+    "rbffd_lu_solve": (C.c_int, [vp, vp, vp, vp]),
+    "rbffd_lu_bytes": (C.c_int64, [vp]),
+    "rbffd_lu_destroy": (None, [vp]),
     "rbffd_morton_order": (C.c_int, [vp, C.c_int64, vp, vp]),
     "rbffd_rcm_order": (C.c_int, [vp, vp, vp]),
     "rbffd_rcm_order_host": (C.c_int, [vp, vp, C.c_int64, vp]),

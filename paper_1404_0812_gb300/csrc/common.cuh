@@ -75,6 +75,34 @@ struct GroupInfo {
     int64_t ell_off[RBFFD_MAX_GROUPS + 1];     // element offsets
 };
 
+// Bounded grid barrier of a cooperative launch (all blocks co-resident):
+// every block adds 1 to *bar and waits until it reaches target (which grows
+// by gridDim.x per barrier).  A block that has polled for about a second, or
+// that sees *err set, gives up, sets *err and returns false, so that no wait
+// can hang; the caller then leaves the kernel.
+constexpr long long GRID_SYNC_MAX_POLLS = 20000000;   // ~1-2 s with 32 ns sleeps
+__device__ __forceinline__ bool grid_sync(unsigned long long* bar, unsigned long long target, int* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1ull);
+        long long polls = 0;
+        while (*((volatile unsigned long long*)bar) < target) {
+            if (++polls > GRID_SYNC_MAX_POLLS || *((volatile int*)err)) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 // exclusive prefix sum of n int32 values on the device (knn.cu)
 rbffd_status exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
 
@@ -106,6 +134,17 @@ struct rbffd_op {
     int32_t* status;            // N
     rbffd_step_ws* step;        // lazily created stepping workspace
     double phase_ms[4];         // device time of build phases (events)
+};
+
+// banded LU of alpha I - beta L_X (lu.cu)
+struct rbffd_lu {
+    int64_t N, kl, ku, ldab;
+    int dtype;                  // RBFFD_F32 / RBFFD_F64
+    double alpha, beta;
+    void* ab;                   // ldab x N band: factor rows above the diagonal
+    void* lmul;                 // kl x N multipliers
+    void* udiag;                // N
+    int32_t* piv;               // N
 };
 
 struct rbffd_mlp {
@@ -142,5 +181,15 @@ rbffd_status build_search_dd(rbffd_op* op, const double* nodes, const double* no
 rbffd_status mlp_guess(const rbffd_op* op, const double* nodes, const double* normals,
                        const rbffd_build_opts& o, float* guess_rows, cudaStream_t st);
 void step_ws_free(rbffd_step_ws* ws);
+// lu.cu: bandwidths of op's matrix in node order; the banded LU of
+// alpha I - beta L_X; the substitutions of one step for nspecies systems,
+// the factor chosen on the device by the SBDF order in *ord_flag (1..4; NULL
+// means order 1, i.e. fac[0]); vectors of vec_dtype, which may differ from
+// the factors' (ywork: 2 N values of the factors' dtype, else unused)
+rbffd_status op_bandwidth(const rbffd_op* op, int64_t* kl, int64_t* ku, cudaStream_t st);
+rbffd_status lu_factor(const rbffd_op* op, double alpha, double beta, int dtype, cudaStream_t st, rbffd_lu** out);
+rbffd_status lu_solve_step(rbffd_lu* const (&fac)[4][2], int nspecies, const void* const b[2], void* const x[2],
+                           int vec_dtype, const int* ord_flag, void* ywork, cudaStream_t st);
+void lu_free(rbffd_lu* lu);
 int sm_count();
 }  // namespace rbffd

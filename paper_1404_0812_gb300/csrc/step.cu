@@ -32,7 +32,7 @@ struct rbffd_step_ws {
     double* partial;               // phases x blocks x 8
     unsigned long long* bar;       // barrier counter
     int* flags;                    // [0] error (timeout), [1] not converged, [2] has_history,
-                                   // [3] report slot of the next step
+                                   // [3] report slot of the next step, [4] order of the last step
     int* rep;                      // per step: iters_u, iters_v, failed
     double* rep_res;               // per step: relres_u, relres_v
     double* tstart;                // time of u at the start of the call (device copy)
@@ -42,6 +42,10 @@ struct rbffd_step_ws {
     cudaStream_t cap;                 // library-owned stream used only for capture
     unsigned char graph_args[1024];   // kernel arguments the graph holds
     size_t graph_args_size;
+    int solver;                       // solver the graph was captured with
+    rbffd_lu* lu[4][2];               // banded LU factors by SBDF order and species
+    rbffd_lu* graph_lu[4][2];         // the factors the captured graph's solve reads
+    double* ywork;                    // 2 N float64: the LU substitutions' forward results
 };
 
 namespace rbffd {
@@ -57,6 +61,9 @@ void step_ws_free(rbffd_step_ws* ws) {
     cudaFree(ws->tstart);
     if (ws->graph) cudaGraphExecDestroy(ws->graph);
     if (ws->cap) cudaStreamDestroy(ws->cap);
+    for (auto& row : ws->lu)
+        for (rbffd_lu* f : row) lu_free(f);
+    cudaFree(ws->ywork);
     delete ws;
 }
 
@@ -64,7 +71,6 @@ namespace {
 
 constexpr int NPHASE = 6;
 constexpr int NSLOT = 8;
-constexpr long long MAX_POLLS = 20000000;   // ~1-2 s with 32 ns sleeps
 
 template <typename T>
 struct Args {
@@ -93,40 +99,18 @@ struct Args {
     int* flags;
     int* rep;
     double* rep_res;
+    int rhs_only;      // 1: form the right-hand side b only (a direct solve follows)
 };
 
 enum { VB = 0, VR = 1, VRH = 2, VP = 3, VQ = 4, VS = 5, VT = 6 };
 
 template <typename T>
-__device__ __forceinline__ T* V(const Args<T>& a, int sp, int k) {
+__host__ __device__ __forceinline__ T* V(const Args<T>& a, int sp, int k) {
     return a.vec + ((int64_t)sp * 7 + k) * a.N;
 }
 
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
-
-// bounded grid barrier: the target grows by gridDim.x per call
-__device__ bool grid_sync(unsigned long long* bar, unsigned long long target, int* err) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        __threadfence();
-        atomicAdd(bar, 1ull);
-        long long polls = 0;
-        while (*((volatile unsigned long long*)bar) < target) {
-            if (++polls > MAX_POLLS || *((volatile int*)err)) {
-                ok = 0;
-                atomicExch(err, 1);
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
 
 // block-reduce K doubles into partial[phase][block][0..K-1]
 template <int K>
@@ -337,6 +321,20 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
         block_partial<6>(d, a.partial, 0);
     }
     if (!grid_sync(a.bar, target += gridDim.x, a.flags)) return;
+    if (a.rhs_only) {
+        // the implicit systems are solved by the banded LU launch that
+        // follows (every block has read flags[2..3] before the barrier)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            int* rp = a.rep + (int64_t)slot * 3;
+            rp[0] = rp[1] = rp[2] = 0;
+            a.rep_res[(int64_t)slot * 2] = 0.0;
+            a.rep_res[(int64_t)slot * 2 + 1] = 0.0;
+            a.flags[2] = min(nhist + 1, max(a.order - 1, 1));
+            a.flags[3] = slot + 1;
+            a.flags[4] = ord;
+        }
+        return;
+    }
     double tot[6];
     grid_total<6>(a.partial, 0, tot);
 
@@ -538,6 +536,7 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
         if (bad) atomicExch(a.flags + 1, 1);
         a.flags[2] = min(nhist + 1, max(a.order - 1, 1));   // past levels now stored
         a.flags[3] = slot + 1;   // every block read the slot before the first barrier
+        a.flags[4] = ord;
     }
 }
 
@@ -586,6 +585,7 @@ void fill_args(Args<T>& a, rbffd_op* op, rbffd_state* s, const rbffd_step_params
     a.flags = ws->flags;
     a.rep = ws->rep;
     a.rep_res = ws->rep_res;
+    a.rhs_only = p->solver == RBFFD_SOLVER_BANDED_LU ? 1 : 0;
 }
 
 template <typename T>
@@ -596,6 +596,15 @@ rbffd_status launch_step(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
     RBFFD_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ws->blocks),
                                                dim3(ws->threads), args, 0, st));
     note_launch();
+    if (a.rhs_only) {
+        // (c0 I - cl delta L) x = b by the cached LU factors of the step's
+        // order (read on the device from flags[4]); x overwrites u, v
+        const void* b[2] = {V(a, 0, VB), a.ns == 2 ? V(a, 1, VB) : nullptr};
+        void* x[2] = {a.u, a.ns == 2 ? a.v : nullptr};
+        rbffd_status r = lu_solve_step(ws->lu, a.ns, b, x, std::is_same<T, float>::value ? RBFFD_F32 : RBFFD_F64,
+                                       ws->flags + 4, ws->ywork, st);
+        if (r != RBFFD_OK) return r;
+    }
     return RBFFD_OK;
 }
 
@@ -610,7 +619,10 @@ rbffd_status run_steps(Args<T>& a, rbffd_step_ws* ws, int64_t nsteps, bool use_g
         }
         return RBFFD_OK;
     }
-    if (!ws->graph || ws->graph_args_size != sizeof(a) || memcmp(ws->graph_args, &a, sizeof(a)) != 0) {
+    // the graph holds the kernels' arguments, the LU solve's factor pointers
+    // included: any change recaptures it
+    if (!ws->graph || ws->graph_args_size != sizeof(a) || memcmp(ws->graph_args, &a, sizeof(a)) != 0 ||
+        ws->solver != a.rhs_only || memcmp(ws->graph_lu, ws->lu, sizeof(ws->lu)) != 0) {
         if (ws->graph) {
             cudaGraphExecDestroy(ws->graph);
             ws->graph = nullptr;
@@ -629,6 +641,8 @@ rbffd_status run_steps(Args<T>& a, rbffd_step_ws* ws, int64_t nsteps, bool use_g
         RBFFD_CUDA_TRY(e);
         memcpy(ws->graph_args, &a, sizeof(a));
         ws->graph_args_size = sizeof(a);
+        ws->solver = a.rhs_only;
+        memcpy(ws->graph_lu, ws->lu, sizeof(ws->lu));
     }
     for (int64_t k = 0; k < nsteps; ++k) {
         RBFFD_CUDA_TRY(cudaGraphLaunch(ws->graph, st));
@@ -661,6 +675,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
                                   (p->nspecies == 1 || (s->v_prev3 && s->g_prev3))),
                     "SBDF4 needs u_prev3 / f_prev3 (and v_prev3 / g_prev3)");
     RBFFD_CHECK_ARG(s->has_history >= 0, "has_history must be >= 0");
+    RBFFD_CHECK_ARG(p->solver == RBFFD_SOLVER_BICGSTAB || p->solver == RBFFD_SOLVER_BANDED_LU, "solver");
     cudaStream_t st = as_stream(stream);
     const size_t elem = p->dtype == RBFFD_F32 ? 4 : 8;
     rbffd_step_ws* ws = op->step;
@@ -696,7 +711,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         RBFFD_CUDA_TRY(cudaMalloc(&ws->vec, 2 * 7 * op->N * elem));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->partial, (size_t)NPHASE * ws->blocks * NSLOT * sizeof(double)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->bar, sizeof(unsigned long long)));
-        RBFFD_CUDA_TRY(cudaMalloc(&ws->flags, 4 * sizeof(int)));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->flags, 5 * sizeof(int)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->tstart, sizeof(double)));
         ws->rep_cap = 0;
     }
@@ -708,7 +723,40 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         RBFFD_CUDA_TRY(cudaMalloc(&ws->rep_res, ws->rep_cap * 2 * sizeof(double)));
     }
     const int kept = std::max(order - 1, 1);   // past levels the order stores
-    int hflags[4] = {0, 0, std::min(s->has_history, kept), 0};   // slot counter starts at 0
+    int hflags[5] = {0, 0, std::min(s->has_history, kept), 0, 0};   // slot counter starts at 0
+    if (p->solver == RBFFD_SOLVER_BANDED_LU) {
+        // factor (c0 I - cl delta L) for every SBDF order this call steps
+        // with (orders climb while history builds up) and species, once per
+        // (order, dt, delta, dtype); factors live with the workspace
+        int h = std::min(s->has_history, kept);
+        bool need[4] = {false, false, false, false};
+        for (int64_t k = 0; k < nsteps && k < 4; ++k) {
+            need[std::min(order, h + 1) - 1] = true;
+            h = std::min(h + 1, kept);
+        }
+        if (nsteps > 4) need[std::min(order, h + 1) - 1] = true;
+        const double c0s[4] = {1.0, 3.0, 11.0, 25.0}, cls[4] = {1.0, 2.0, 6.0, 12.0};
+        const double del[2] = {p->delta_u, p->delta_v};
+        for (int o = 0; o < 4; ++o) {
+            if (!need[o]) continue;
+            for (int sp = 0; sp < p->nspecies; ++sp) {
+                const double alpha = c0s[o], beta = cls[o] * p->dt * del[sp];
+                rbffd_lu*& f = ws->lu[o][sp];
+                // float64 factors whatever the step's dtype: a float32 band
+                // LU loses several digits to its growth and rounding, while
+                // the substitutions are latency-bound, not FP64-bound
+                if (f && (f->alpha != alpha || f->beta != beta)) {
+                    lu_free(f);
+                    f = nullptr;
+                }
+                if (!f) {
+                    rbffd_status fs = lu_factor(op, alpha, beta, RBFFD_F64, st, &f);
+                    if (fs != RBFFD_OK) return fs;
+                }
+            }
+        }
+        if (!ws->ywork) RBFFD_CUDA_TRY(cudaMalloc(&ws->ywork, 2 * op->N * sizeof(double)));
+    }
     RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, st));
     RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->tstart, &s->t, sizeof(double), cudaMemcpyHostToDevice, st));
     RBFFD_CUDA_TRY(cudaMemsetAsync(ws->rep, 0, ws->rep_cap * 3 * sizeof(int), st));
@@ -727,7 +775,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
     if (rs != RBFFD_OK) return rs;
     std::vector<int> rep(std::max<int64_t>(nsteps, 1) * 3);
     std::vector<double> res(std::max<int64_t>(nsteps, 1) * 2);
-    RBFFD_CUDA_TRY(cudaMemcpyAsync(hflags, ws->flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(hflags, ws->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     if (nsteps > 0) {
         RBFFD_CUDA_TRY(cudaMemcpyAsync(rep.data(), ws->rep, nsteps * 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
         RBFFD_CUDA_TRY(cudaMemcpyAsync(res.data(), ws->rep_res, nsteps * 2 * sizeof(double),

@@ -268,3 +268,26 @@ def test_schnakenberg_kinetics_every_term():
     cg = _monomials(lambda u, v: ostp.reaction(p, u, v)[1])
     np.testing.assert_allclose(cf, _expect({(0, 0): g * a, (1, 0): -g, (2, 1): g}), atol=1e-13)
     np.testing.assert_allclose(cg, _expect({(0, 0): g * b, (2, 1): -g}), atol=1e-13)
+
+
+def test_sparse_lu_solver_matches_dense_and_bicgstab(op642):
+    """Section 7's direct solves: the oracle's sparse-LU SBDF2 steps equal the
+    same steps with each implicit system solved densely (numpy), and the
+    BiCGSTAB steps to their tolerance; the sparse matrix is the operator's."""
+    ns, op = op642
+    L = oop.sparse_matrix(op, ns.N)
+    Ld = oop.dense(op, ns.N)
+    assert np.array_equal(L.toarray(), Ld)
+    s = W.SCHNAKENBERG
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    lu = ostp.imex_run(lambda x: oop.apply(op, x), u0, v0, s, 20, solver="lu", L_matrix=L)
+    bi = ostp.imex_run(lambda x: oop.apply(op, x), u0, v0, s, 20, tol=1e-14)
+    assert all(i == (0, 0) for i in lu["iters"])
+    for k in ("u", "v"):
+        assert np.abs(lu[k] - bi[k]).max() <= 1e-11 * np.abs(bi[k]).max()
+    # one SBDF1 step by hand with a dense solve
+    f, g = ostp.reaction(s, u0, v0)
+    M = np.eye(ns.N) - s["dt"] * s["delta_u"] * Ld
+    one = ostp.imex_run(lambda x: oop.apply(op, x), u0, v0, s, 1, solver="lu", L_matrix=L)
+    ref = np.linalg.solve(M, u0 + s["dt"] * f)
+    assert np.abs(one["u"] - ref).max() <= 1e-13 * np.abs(ref).max()
