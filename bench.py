@@ -75,6 +75,9 @@ def _parse():
     ap.add_argument("--profile", action="store_true", help="one small run for ncu (NVTX 'profiled')")
     ap.add_argument("--profile-n", type=int, default=40_000, help="nodes of the --profile case")
     ap.add_argument("--profile-plain", action="store_true", help="--profile without the learned start")
+    ap.add_argument("--horizons", action="store_true",
+                    help="the long-horizon stepping studies only (C2 5000 steps, the 2M-node Gray-Scott "
+                         "stand-in 10k steps in float32 and float64); one JSON line")
     return ap.parse_args()
 
 
@@ -268,8 +271,10 @@ def configs_report(R, W, T, torch, nets):
     (not part of the headline value).  A configuration that fails reports
     its error instead of its numbers."""
     out = {}
-    for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2), ("bumpy500k_learned", _c4),
-                     ("bumpy2m_pointcloud", _c5), ("reorder_1m_shuffled", _reorder),
+    for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2),
+                     ("torus40k_direct_lu_vs_bicgstab", _c2_lu), ("bumpy500k_learned", _c4),
+                     ("bumpy2m_pointcloud", _c5), ("bumpy2m_analytic_gray_scott", _c5_standin),
+                     ("reorder_1m_shuffled", _reorder),
                      ("sphere_heat_convergence_bdf4", _e3),
                      ("forced_sphere_convergence_bdf4", _e4), ("forced_torus_convergence_bdf4", _e5),
                      ("forced_fixed_kappa_1e14", _e6), ("forced_fixed_kappa_1e20_dd", _e6_dd)):
@@ -502,42 +507,97 @@ def _c1(R, W, T, torch, nets):
     return c1
 
 
-def _c2(R, W, T, torch, nets):
+def _c2(R, W, T, torch, nets, horizon=5000):
     ev = lambda: _ev(torch)
     stream = torch.cuda.current_stream()
     # C2: torus m = 82 (N = 40,344), n = 50, IMQ; Schnakenberg, float32 vs
-    # float64 stepping (100 steps compared; 5000 float32 steps timed)
+    # float64 stepping over the whole 5000-step horizon (the difference after
+    # 100 steps is the parity figure; the full-horizon one is reported as is:
+    # pattern formation amplifies rounding differences)
     ns = W.torus_staggered(82)
     op = R.build_operator(T(ns.X), T(ns.normals), 50, kernel="imq", kappa_target=KAPPA_T)
     s = W.SCHNAKENBERG
     name, coef = R.model_coefs(s)
     u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
-    res = {}
+    st, ms, d = {}, {}, {}
     for dt_, tol in ((torch.float64, 1e-12), (torch.float32, 1e-8)):
-        st = R.StepState.create(T(u0, dt_), T(v0, dt_))
-        p = R.StepParams(model=name, nspecies=2, dtype=dt_, dt=s["dt"], delta_u=s["delta_u"],
-                         delta_v=s["delta_v"], coef=coef, tol=tol, use_graph=True)
-        a, b = ev()
-        a.record(stream)
-        R.step_imex(op, st, p, 100)
-        b.record(stream)
-        torch.cuda.synchronize()
-        res[dt_] = (st, a.elapsed_time(b) / 100)
-    d = float((res[torch.float32][0].u.double() - res[torch.float64][0].u).abs().max()
-              / res[torch.float64][0].u.abs().max())
-    st = res[torch.float32][0]
-    p = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
-                     delta_v=s["delta_v"], coef=coef, tol=1e-6, use_graph=True)
-    a, b = ev()
-    a.record(stream)
-    R.step_imex(op, st, p, 4900)
-    b.record(stream)
-    torch.cuda.synchronize()
-    return {"f32_vs_f64_rel_linf_100_steps": d,
-                                    "ms_per_step_f64": round(res[torch.float64][1], 4),
-                                    "ms_per_step_f32": round(res[torch.float32][1], 4),
-                                    "ms_per_step_f32_steps_101_5000": round(a.elapsed_time(b) / 4900, 4),
-                                    "u_range_at_5000": [float(st.u.min()), float(st.u.max())]}
+        st[dt_] = R.StepState.create(T(u0, dt_), T(v0, dt_))
+        ms[dt_] = 0.0
+    p = {dt_: R.StepParams(model=name, nspecies=2, dtype=dt_, dt=s["dt"], delta_u=s["delta_u"],
+                           delta_v=s["delta_v"], coef=coef, tol=tol, use_graph=True)
+         for dt_, tol in ((torch.float64, 1e-12), (torch.float32, 1e-8))}
+    done = 0
+    for upto in (100, horizon):
+        for dt_ in (torch.float64, torch.float32):
+            a, b = ev()
+            a.record(stream)
+            R.step_imex(op, st[dt_], p[dt_], upto - done)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms[dt_] += a.elapsed_time(b)
+        done = upto
+        d[upto] = {k: float((getattr(st[torch.float32], k).double() - getattr(st[torch.float64], k)).abs().max()
+                            / getattr(st[torch.float64], k).abs().max()) for k in ("u", "v")}
+    u64 = st[torch.float64].u
+    return {"f32_vs_f64_rel_linf_100_steps": max(d[100].values()),
+            f"f32_vs_f64_rel_linf_{horizon}_steps": max(d[horizon].values()),
+            "by_species": {str(k): v for k, v in d.items()},
+            "ms_per_step_f64": round(ms[torch.float64] / horizon, 4),
+            "ms_per_step_f32": round(ms[torch.float32] / horizon, 4),
+            f"u_range_at_{horizon}_f64": [float(u64.min()), float(u64.max())]}
+
+
+def _c2_lu(R, W, T, torch, nets, steps=100):
+    """Section 7's direct solves against BiCGSTAB on the C2 torus (N = 40,344,
+    n = 50, Schnakenberg SBDF2): nodes renumbered by reverse Cuthill-McKee
+    (rbffd_rcm_order), the SBDF matrices factorised once as banded LU
+    (float64 factors), then ms per step of the LU path and of BiCGSTAB
+    (float32 and float64 state, CUDA graph) and the difference of their
+    solutions after `steps` steps."""
+    ns = W.torus_staggered(82)
+    op0 = R.build_operator(T(ns.X), T(ns.normals), 50, kernel="imq", kappa_target=KAPPA_T)
+    perm = R.rcm_order(op0).cpu().numpy()
+    del op0
+    X, Nr = ns.X[perm].copy(), ns.normals[perm].copy()
+    op = R.build_operator(T(X), T(Nr), 50, kernel="imq", kappa_target=KAPPA_T)
+    kl, ku = R.op_bandwidth(op)
+    s = W.SCHNAKENBERG
+    name, coef = R.model_coefs(s)
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+    u0, v0 = u0[perm].copy(), v0[perm].copy()
+    out = {"N": ns.N, "bandwidths": [kl, ku]}
+    t0 = time.perf_counter()
+    lu = R.lu_factor(op, 3.0, 2 * s["dt"] * s["delta_v"])
+    out["factor_s_one_matrix_f64"] = round(time.perf_counter() - t0, 3)
+    out["factor_bytes_one_matrix"] = lu.bytes
+    del lu
+    res = {}
+    for dt_, tol in ((torch.float32, 1e-6), (torch.float64, 1e-12)):
+        for solver in ("lu", "bicgstab"):
+            p = R.StepParams(model=name, nspecies=2, dtype=dt_, dt=s["dt"], delta_u=s["delta_u"],
+                             delta_v=s["delta_v"], coef=coef, tol=tol, use_graph=True, solver=solver)
+            st = R.StepState.create(T(u0, dt_), T(v0, dt_))
+            t1 = time.perf_counter()
+            R.step_imex(op, st, p, 2)      # SBDF1 + SBDF2 factors, graph capture
+            torch.cuda.synchronize()
+            setup = time.perf_counter() - t1
+            a, b = _ev(torch)
+            a.record()
+            rep = R.step_imex(op, st, p, steps)
+            b.record()
+            torch.cuda.synchronize()
+            key = f"{solver}_{'f32' if dt_ == torch.float32 else 'f64'}"
+            out[f"ms_per_step_{key}"] = round(a.elapsed_time(b) / steps, 4)
+            if solver == "bicgstab":
+                out[f"iters_mean_{key}"] = round(rep["total_iters"] / steps / 2, 2)
+            else:
+                out[f"first_two_steps_s_{key}"] = round(setup, 3)
+            res[key] = st.u.double()
+    for k in ("f32", "f64"):
+        out[f"lu_vs_bicgstab_rel_linf_{k}"] = float((res[f"lu_{k}"] - res[f"bicgstab_{k}"]).abs().max()
+                                                    / res[f"bicgstab_{k}"].abs().max())
+        out[f"lu_over_bicgstab_time_{k}"] = round(out[f"ms_per_step_lu_{k}"] / out[f"ms_per_step_bicgstab_{k}"], 2)
+    return out
 
 
 def _c4(R, W, T, torch, nets):
@@ -612,6 +672,64 @@ def _c5(R, W, T, torch, nets):
     return out
 
 
+def _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=None):
+    """The largest stable stand-in of the point-cloud configuration: the
+    bumpy sphere at N = 2,000,000 with analytic normals and no jitter (the
+    jittered PCA-normal cloud has eigenvalues of L_X far in the right
+    half-plane, see test_pointcloud_spectrum), n = 70, learned build;
+    Gray-Scott in float32 for `steps` steps (ms per step), float64 beside it
+    for the parity window (100 steps) and, with f64_steps, up to that
+    horizon for the full-horizon difference."""
+    ns = W.bumpy_sphere(2_000_000, jitter=0.0, seed=4, normals="analytic")
+    op = R.build_operator(T(ns.X), T(ns.normals), 70, kernel="imq", kappa_target=KAPPA_T,
+                          mlps=[nets[SIZES.index(70)]], allow_failures=True)
+    info = R.get_stencil_info(op)
+    g = W.GRAY_SCOTT
+    name, coef = R.model_coefs(g)
+    u0, v0 = W.gray_scott_initial(ns.X, seed=5, spots=50, radius=0.05)
+    out = {"stencils_ok_fraction": round(float(((info["status"] == 0) | (info["status"] == 4)).double().mean()), 6),
+           "build_ms": round(sum(R.get_build_timings(op).values()), 1)}
+    st, p = {}, {}
+    for dt_, tol in ((torch.float32, 1e-6), (torch.float64, 1e-12)):
+        st[dt_] = R.StepState.create(T(u0, dt_), T(v0, dt_))
+        p[dt_] = R.StepParams(model=name, nspecies=2, dtype=dt_, dt=g["dt"], delta_u=g["delta_u"],
+                              delta_v=g["delta_v"], coef=coef, tol=tol, use_graph=True)
+    diffs = {}
+    done = {torch.float32: 0, torch.float64: 0}
+    ms32 = 0.0
+    marks = [100] + ([f64_steps] if f64_steps else [])
+    for upto in marks:
+        for dt_ in (torch.float32, torch.float64):
+            a, b = _ev(torch)
+            a.record()
+            rep = R.step_imex(op, st[dt_], p[dt_], upto - done[dt_], allow_failure=True)
+            b.record()
+            torch.cuda.synchronize()
+            if dt_ == torch.float32:
+                ms32 += a.elapsed_time(b)
+            done[dt_] = upto
+            if rep["status"] != 0:
+                out[f"solver_failure_{'f32' if dt_ == torch.float32 else 'f64'}"] = rep
+        diffs[upto] = max(float((getattr(st[torch.float32], k).double() - getattr(st[torch.float64], k)).abs().max()
+                                / getattr(st[torch.float64], k).abs().max()) for k in ("u", "v"))
+    if steps > done[torch.float32]:
+        a, b = _ev(torch)
+        a.record()
+        rep = R.step_imex(op, st[torch.float32], p[torch.float32], steps - done[torch.float32], allow_failure=True)
+        b.record()
+        torch.cuda.synchronize()
+        ms32 += a.elapsed_time(b)
+        if rep["status"] != 0:
+            out["solver_failure_f32"] = rep
+    out["f32_vs_f64_rel_linf"] = {str(k): v for k, v in diffs.items()}
+    out["steps_f32"] = steps
+    out["ms_per_step_f32"] = round(ms32 / steps, 4)
+    u = st[torch.float32].u
+    out["u_range_f32_end"] = [float(u.min()), float(u.max())]
+    out["finite_f32_end"] = bool(torch.isfinite(u).all().item())
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -627,7 +745,7 @@ def run_ours(args):
     T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
 
     cpu = None
-    if rank == 0 and not args.profile:   # oracle sample first, before heavy GPU work
+    if rank == 0 and not (args.profile or args.horizons):   # oracle sample first, before heavy GPU work
         cpu1 = run_cpu_sample(args.sample, 1234)
         cpu = run_cpu_sample(args.sample, 1234, host_cores())
     n_nodes = args.profile_n if args.profile else N_NODES
@@ -655,6 +773,15 @@ def run_ours(args):
         st = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
         R.step_imex(op, st, sp, 1)
         return op
+
+    if args.horizons:
+        t0 = time.perf_counter()
+        out = {"horizons": True,
+               "torus40k_schnakenberg": _c2(R, W, T, torch, nets),
+               "bumpy2m_analytic_gray_scott": _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=10_000)}
+        out["wall_s"] = round(time.perf_counter() - t0, 1)
+        print(json.dumps(out))
+        return
 
     if args.profile:
         for _ in range(2):
@@ -709,10 +836,18 @@ def run_ours(args):
         torch.distributed.barrier()
     ms = max_over_ranks(statistics.mean(times), dev)
 
-    # end to end through the public API from pinned host memory
+    # end to end through the public API: the step's inputs go up from
+    # pinned host memory, and the product of the build -- the operator as
+    # sliced ELL (int32 indices and float64 weights, padding included) and
+    # the per-node eps -- comes back into pinned host memory, all inside the
+    # timed region
     hX = torch.from_numpy(ns.X).pin_memory()
     hN = torch.from_numpy(ns.normals).pin_memory()
     hP = torch.from_numpy(nper).pin_memory()
+    elems = R.get_ell(op)["elems"]
+    hI = torch.empty(elems, dtype=torch.int32).pin_memory()
+    hW = torch.empty(elems, dtype=torch.float64).pin_memory()
+    hE = torch.empty(N_NODES, dtype=torch.float64).pin_memory()
     e2e_times = []
     for _ in range(max(1, min(args.steps, 3))):
         flush.fill_(1.0)
@@ -722,11 +857,28 @@ def run_ours(args):
         Nd = hN.to(dev, non_blocking=True)
         Pd = hP.to(dev, non_blocking=True)
         op = one_step(Xd, Nd, Pd)
-        eps_host = R.get_stencil_info(op)["eps"].cpu()
+        ell = R.get_ell(op)
+        hI.copy_(ell["idx"], non_blocking=True)
+        hW.copy_(ell["w64"], non_blocking=True)
+        hE.copy_(R.get_eps(op)[0], non_blocking=True)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     h2d = hX.numel() * 8 + hN.numel() * 8 + hP.numel() * 4
-    d2h = eps_host.numel() * 8
+    d2h = hI.numel() * 4 + hW.numel() * 8 + hE.numel() * 8
+    # the same step without the networks (the plain eps search), timed once
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    op_p = R.build_operator(X, Nr, NP, kernel="imq", kappa_target=KAPPA_T,
+                            block_threads=shape["block_threads"], blocks_per_sm=shape["blocks_per_sm"])
+    stp = R.StepState.create(T(u0, torch.float32), T(v0, torch.float32))
+    R.step_imex(op_p, stp, sp, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_step_ms = e0.elapsed_time(e1)
+    del op_p, stp
 
     info = {k: v.cpu().numpy() for k, v in R.get_stencil_info(op).items()}
     ok = bool(np.all((info["status"] == 0) | (info["status"] == 4)))
@@ -828,7 +980,16 @@ def run_ours(args):
         "all_stencils_ok": ok,
         "other_configs": configs,
         "e2e": {"value": round(N_NODES / statistics.mean(e2e_times), 1), "unit": UNIT,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "returned": "the built operator (sliced ELL: int32 indices + float64 weights) and eps"},
+        "rates": {"learned_start_in_distribution": round(value, 1),
+                  "plain_search_no_networks": round(N_NODES / (plain_step_ms * 1e-3), 1),
+                  "learned_start_held_out_bumpy500k":
+                      (configs or {}).get("bumpy500k_learned", {}).get("stencils_per_s_learned_build"),
+                  "held_out_accepted_fraction":
+                      (configs or {}).get("bumpy500k_learned", {}).get("learned", {}).get("accepted_fraction"),
+                  "note": "value = the learned start on the networks' own distribution (networks trained on "
+                          "Fibonacci spheres and tori); the plain search and the held-out bumpy sphere beside it"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "cpu_baseline": {"value": round(cpu_value, 3), "unit": UNIT, "cores": cpu["procs"], "kind": "oracle",

@@ -1,7 +1,7 @@
 // FP64 throughput microbenchmarks.  rbffd_fp64_peak (FMA on the FP64 pipe)
 // is the denominator of the build's roofline ("alu" bound): each thread runs
 // 8 independent FMA chains.  rbffd_fp64_mma_peak measures the FP64 tensor
-// path (warp-level mma.sync m16n8k16 f64, 4 independent accumulators per
+// path (warp-level mma.sync m16n8k16 f64, 8 independent accumulators per
 // warp), the only FP64 matrix instruction of this architecture, to show
 // whether moving the build's small factorisations onto it could pay.
 #include "common.cuh"
@@ -23,20 +23,21 @@ __global__ void fp64_fma_loop(double* out, int iters, double a, double b) {
     if (s == 12345.678) out[0] = s;   // keeps the chains alive
 }
 
-// D = A B + D on 16 x 8 tiles with k = 16, four independent accumulators
+// D = A B + D on 16 x 8 tiles with k = 16, eight independent accumulators
+// (eight MMAs in flight per warp, 64 warps per SM: no dependency stall)
 __global__ void fp64_mma_loop(double* out, int iters) {
-    double a[8], b[4], c[4][4];
+    double a[8], b[4], c[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i) a[i] = 1e-3 * (threadIdx.x + i);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = 1e-3 * ((int)threadIdx.x - i);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 8; ++q)
 #pragma unroll
         for (int i = 0; i < 4; ++i) c[q][i] = 0.0;
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 8; ++q)
             asm volatile(
                 "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
                 "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};"
@@ -46,7 +47,7 @@ __global__ void fp64_mma_loop(double* out, int iters) {
     }
     double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 8; ++q)
 #pragma unroll
         for (int i = 0; i < 4; ++i) s += c[q][i];
     if (s == 12345.678) out[0] = s;   // keeps the chains alive
@@ -114,9 +115,9 @@ extern "C" rbffd_status rbffd_fp64_mma_peak(void* stream, double* gflops) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(out, st);
-    // 2 * 16 * 8 * 16 flops per warp-level mma, 4 per iteration per warp
+    // 2 * 16 * 8 * 16 flops per warp-level mma, 8 per iteration per warp
     const double warps = (double)blocks * threads / 32.0;
-    double flops = 2.0 * 16.0 * 8.0 * 16.0 * 4.0 * (double)iters * warps;
+    double flops = 2.0 * 16.0 * 8.0 * 16.0 * 8.0 * (double)iters * warps;
     *gflops = flops / (best * 1e-3) / 1e9;
     return RBFFD_OK;
 }
