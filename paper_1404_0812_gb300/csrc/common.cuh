@@ -145,6 +145,8 @@ struct rbffd_lu {
     void* lmul;                 // kl x N multipliers
     void* udiag;                // N
     int32_t* piv;               // N
+    void* work;                 // 2 N + 16 values: b and y of rbffd_lu_solve
+    int* err;                   // device flag: a bounded wait of the solve gave up
 };
 
 struct rbffd_mlp {
@@ -185,11 +187,12 @@ void step_ws_free(rbffd_step_ws* ws);
 // alpha I - beta L_X; the substitutions of one step for nspecies systems,
 // the factor chosen on the device by the SBDF order in *ord_flag (1..4; NULL
 // means order 1, i.e. fac[0]); vectors of vec_dtype, which may differ from
-// the factors' (ywork: 2 N values of the factors' dtype, else unused)
+// the factors'; work: per species 2 N + 16 values of the factors' dtype plus
+// 64 bytes; *err set when a bounded wait gave up
 rbffd_status op_bandwidth(const rbffd_op* op, int64_t* kl, int64_t* ku, cudaStream_t st);
 rbffd_status lu_factor(const rbffd_op* op, double alpha, double beta, int dtype, cudaStream_t st, rbffd_lu** out);
 rbffd_status lu_solve_step(rbffd_lu* const (&fac)[4][2], int nspecies, const void* const b[2], void* const x[2],
-                           int vec_dtype, const int* ord_flag, void* ywork, cudaStream_t st);
+                           int vec_dtype, const int* ord_flag, void* work, int* err, cudaStream_t st);
 void lu_free(rbffd_lu* lu);
 int sm_count();
 }  // namespace rbffd

@@ -38,13 +38,15 @@ void lu_free(rbffd_lu* lu) {
     cudaFree(lu->lmul);
     cudaFree(lu->udiag);
     cudaFree(lu->piv);
+    cudaFree(lu->work);
+    cudaFree(lu->err);
     delete lu;
 }
 
 namespace {
 
-constexpr int FACTOR_THREADS = 256;
-constexpr int SOLVE_THREADS = 1024;
+constexpr int FACTOR_THREADS = 1024;
+constexpr int SOLVE_THREADS = 256;
 
 __global__ void bandwidth_kernel(const int32_t* __restrict__ idx, const int32_t* __restrict__ row_node, GroupInfo gi,
                                  int* __restrict__ out) {
@@ -185,15 +187,29 @@ __global__ void __launch_bounds__(FACTOR_THREADS) factor_kernel(FactorArgs<T> a)
             rp[k] = cj[c];
         }
         __syncthreads();
-        // interchange + rank-1 update, rows c + 1 .. c + rows - 1 (consecutive
-        // threads on consecutive rows of a column)
-        const int64_t nb = rows - 1;
-        for (int64_t e = tid; e < nown * nb; e += FACTOR_THREADS) {
-            const int64_t k = e / nb, t = e - k * nb + 1;
-            const int64_t j = c + 1 + q0 + k * G, i = c + t;
-            T* aij = a.ab + j * ldab + kl + ku + i - j;
-            const T v = i == p ? rp[k] : *aij;
-            *aij = v - l[t - 1] * rc[k];
+        // interchange + rank-1 update, rows c + 1 .. c + rows - 1: consecutive
+        // threads on consecutive rows of a column, four rows per thread
+        // loaded before any is stored (the window lives in L2: four loads
+        // in flight per thread hide its latency)
+        const int nb = (int)(rows - 1);
+        const int pr = (int)(p - c);              // row p as an offset t (0: no interchange)
+        for (int64_t k = 0; k < nown; ++k) {
+            const int64_t j = c + 1 + q0 + k * G;
+            T* __restrict__ cj = a.ab + j * ldab + kl + ku + c - j;   // cj[t] = A(c + t, j)
+            const T u = rc[k], oldc = rp[k];
+            for (int t0 = 1 + tid; t0 <= nb; t0 += 4 * FACTOR_THREADS) {
+                T v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + q * FACTOR_THREADS;
+                    v[q] = t <= nb ? (t == pr ? oldc : cj[t]) : T(0);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + q * FACTOR_THREADS;
+                    if (t <= nb) cj[t] = v[q] - l[t - 1] * u;
+                }
+            }
         }
         for (int64_t k = tid; k < nown; k += FACTOR_THREADS) {
             const int64_t j = c + 1 + q0 + k * G;
@@ -206,18 +222,51 @@ __global__ void __launch_bounds__(FACTOR_THREADS) factor_kernel(FactorArgs<T> a)
 // ---------------------------------------------------------------------------
 // substitutions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async_elem(float* s, const float* g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g));
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
 }
-__device__ __forceinline__ void cp_async_elem(double* s, const double* g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g));
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
 }
-__device__ __forceinline__ void cp_async_elem(int32_t* s, const int32_t* g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g));
+// one bulk copy global -> shared completing on bar (both ends 16-byte aligned,
+// bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
+// bounded wait (about a second at most) for the given phase parity of bar:
+// non-blocking tests with a short sleep between them; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long it = 0; it < GRID_SYNC_MAX_POLLS; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
+
+// the 16-byte-aligned span covering [p, p + bytes): its start and length
+struct Span {
+    const char* src;
+    uint32_t bytes, off;   // off: bytes from the span's start to p
+};
+__device__ __forceinline__ Span span_of(const void* p, size_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t a0 = a & ~(uintptr_t)15, a1 = (a + bytes + 15) & ~(uintptr_t)15;
+    return Span{reinterpret_cast<const char*>(a0), (uint32_t)(a1 - a0), (uint32_t)(a - a0)};
+}
 
 template <typename T>
 struct SolveSys {
@@ -234,128 +283,215 @@ struct SolveArgs {
     TV* x[2];                    //   substitutions run in the factor's)
     int64_t N, kl, ku, ldab;
     const int* ord_flag;         // device: the SBDF order of the current step, or NULL (order 1)
-    T* ywork;                    // 2 N values of T: forward results when TV != T
+    T* work;                     // per species 2 N + 16 values of T: b, then the forward results y
+    int* err;                    // set when a bounded wait gave up
 };
+
+constexpr int SLOT_PAD = 32;     // bytes of alignment slack in a staged column
+
+// bytes of one staging slot: a column of up to KU values plus slack, and two
+// 16-byte scalar spans (pivot or U diagonal; the row entering the window)
+template <typename T>
+__host__ __device__ inline size_t slot_bytes(int64_t KU) {
+    return (((size_t)KU * sizeof(T) + SLOT_PAD + 15) & ~(size_t)15) + 32;
+}
 
 // x = M^{-1} b for species blockIdx.x: forward substitution with the row
 // interchanges and L (column by column), then back substitution with U, in
-// the factor's arithmetic T; b and x are of type TV (float32 vectors of a
-// float32 time step are widened on load and rounded on store, and the
-// forward result y is kept in x only when TV = T, else in ywork).
+// the factor's arithmetic T (b and x of type TV).  Each step's factor
+// column and scalars arrive by bulk copies (TMA) D - 1 steps ahead into D
+// shared-memory slots, each completing on its own mbarrier; the solution's
+// active rows live in a shared-memory ring (slot of row i: i mod (kl + 2)
+// forward, i mod (kl + ku + 2) back), one __syncthreads per step.
 template <typename T, typename TV, int D>
 __global__ void __launch_bounds__(SOLVE_THREADS) solve_kernel(SolveArgs<T, TV> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t N = a.N, kl = a.kl, ku = a.ku, ldab = a.ldab, KU = kl + ku;
-    const int64_t W = KU + 2;                       // ring of the active rows
+    const int W = (int)KU + 2;
     T* win = reinterpret_cast<T*>(smem_raw);
-    T* pf = win + W;                                // D staged columns of KU entries
-    T* ps = pf + D * KU;                            // D staged scalars (U diagonal)
-    T* pe = ps + D;                                 // D staged entering rows
-    TV* pv = reinterpret_cast<TV*>((reinterpret_cast<uintptr_t>(pe + D) + 7) & ~(uintptr_t)7);   // D entering rows of b
-    int32_t* pp = reinterpret_cast<int32_t*>(pv + D);   // D staged pivots
+    unsigned char* slots = smem_raw + (((size_t)W * sizeof(T) + 15) & ~(size_t)15);
+    const size_t SB = slot_bytes<T>(KU);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(slots + D * SB);
     const int tid = threadIdx.x, sp = blockIdx.x;
     const int ord = a.ord_flag ? *((volatile const int*)a.ord_flag) : 1;
     const SolveSys<T> f = a.sys[min(max(ord, 1), 4) - 1][sp];
     const TV* bvec = a.b[sp];
     TV* xo = a.x[sp];
-    T* x = std::is_same<T, TV>::value ? reinterpret_cast<T*>(xo) : a.ywork + sp * N;
+    T* wb = a.work + sp * (2 * N + 16);   // b in T
+    T* wy = wb + N;                       // forward results
+    // where a slot's data lands (offsets into the slot set by the producer)
+    __shared__ uint32_t s_off[D][3];
+    __shared__ int s_err;   // a bounded wait gave up (read after the step's barrier)
+    if (tid == 0) s_err = 0;
+
+    for (int64_t i = tid; i < N; i += SOLVE_THREADS) wb[i] = (T)bvec[i];
+    // every writer orders its generic-proxy writes of wb before the bulk
+    // copies (async proxy) that read them after the barrier
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    if (tid == 0) {
+        for (int k = 0; k < D; ++k) mbar_init(bar + k);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    bool ok = true;
 
     // ---- forward: for c = 0 .. N-1: swap rows c and piv[c], then rows
-    // c+1 .. c+kl -= L(., c) y_c.  Ring slot of row i: i mod (kl + 2).
+    // c+1 .. c+kl -= L(., c) y_c
     {
-        const int64_t W1 = kl + 2;
-        for (int64_t i = tid; i <= min(kl, N - 1); i += SOLVE_THREADS) win[i % W1] = (T)bvec[i];
-        auto issue = [&](int64_t c) {
-            if (c < N) {
-                const int64_t s = c % D;
-                const int64_t lim = min(kl, N - 1 - c);
-                for (int64_t t = tid; t < lim; t += SOLVE_THREADS) cp_async_elem(pf + s * KU + t, f.lmul + c * kl + t);
-                if (tid == 0) {
-                    cp_async_elem(pp + s, f.piv + c);
-                    if (c + 1 + kl < N) cp_async_elem(pv + s, bvec + c + 1 + kl);
-                }
-            }
-            cp_async_commit();
+        const int W1 = (int)kl + 2, KL = (int)kl;
+        for (int64_t i = tid; i <= min(kl, N - 1); i += SOLVE_THREADS) win[i] = wb[i];
+        auto issue = [&](int64_t c) {   // thread 0: stage column c
+            if (c >= N) return;
+            const int s = (int)(c & (D - 1));
+            unsigned char* slot = slots + s * SB;
+            const int lim = (int)min(kl, N - 1 - c);
+            const Span col = span_of(f.lmul + c * kl, (size_t)max(lim, 1) * sizeof(T));
+            const Span pv = span_of(f.piv + c, sizeof(int32_t));
+            const bool enter = c + 1 + kl < N;
+            const Span be = span_of(wb + (enter ? c + 1 + kl : c), sizeof(T));
+            s_off[s][0] = col.off;
+            s_off[s][1] = pv.off;
+            s_off[s][2] = be.off;
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_expect_tx(bar + s, col.bytes + pv.bytes + be.bytes);
+            bulk_g2s(slot, col.src, col.bytes, bar + s);
+            bulk_g2s(slot + SB - 32, pv.src, pv.bytes, bar + s);
+            bulk_g2s(slot + SB - 16, be.src, be.bytes, bar + s);
         };
-        for (int64_t c = 0; c < D - 1; ++c) issue(c);
+        if (tid == 0)
+            for (int64_t c = 0; c < D - 1; ++c) issue(c);
+        __syncthreads();
+        int cs = 0;   // ring slot of row c
         for (int64_t c = 0; c < N; ++c) {
-            cp_async_wait<D - 2>();
-            __syncthreads();
-            const int64_t s = c % D;
-            const int64_t p = pp[s];
-            const T wc = win[c % W1];
-            const T yc = p == c ? wc : win[p % W1];
-            const int64_t lim = min(kl, N - 1 - c);
-            for (int64_t t = tid; t <= kl; t += SOLVE_THREADS) {
-                if (t < lim) {
-                    const int64_t i = c + 1 + t;
-                    const T v = i == p ? wc : win[i % W1];
-                    win[i % W1] = v - pf[s * KU + t] * yc;
-                } else if (t == kl && c + 1 + kl < N) {
-                    win[(c + 1 + kl) % W1] = (T)pv[s];   // the row entering the window
-                }
+            const int s = (int)(c & (D - 1));
+            if (!mbar_wait(bar + s, (uint32_t)((c / D) & 1))) {
+                s_err = 1;
+                atomicExch(a.err, 1);
             }
-            if (tid == 0) x[c] = yc;
-            issue(c + D - 1);
-        }
-        cp_async_wait<0>();
-        __syncthreads();
-    }
-    // ---- back: for j = N-1 .. 0: x_j = y_j / U_jj, rows j-1 .. j-KU -= U(., j) x_j
-    {
-        for (int64_t i = (N - 1 - KU > 0 ? N - 1 - KU : 0) + tid; i < N; i += SOLVE_THREADS) win[i % W] = x[i];
-        auto issue = [&](int64_t j) {
-            if (j >= 0) {
-                const int64_t s = j % D;
-                const int64_t lim = min(KU, j);
-                // U(j - 1 - t, j) = ab[j ldab + KU - 1 - t]
-                for (int64_t t = tid; t < lim; t += SOLVE_THREADS)
-                    cp_async_elem(pf + s * KU + t, f.ab + j * ldab + KU - 1 - t);
-                if (tid == 0) {
-                    cp_async_elem(ps + s, f.udiag + j);
-                    if (j - 1 - KU >= 0) cp_async_elem(pe + s, x + j - 1 - KU);
-                }
-            }
-            cp_async_commit();
-        };
-        __syncthreads();
-        for (int64_t j = N - 1; j > N - 1 - (D - 1); --j) issue(j);
-        for (int64_t j = N - 1; j >= 0; --j) {
-            cp_async_wait<D - 2>();
             __syncthreads();
-            const int64_t s = j % D;
-            const T xj = win[j % W] / ps[s];
-            const int64_t lim = min(KU, j);
-            for (int64_t t = tid; t <= KU; t += SOLVE_THREADS) {
+            if (s_err) {
+                // leave only after the copies already issued have landed (bounded)
+                if (tid == 0)
+                    for (int64_t c2 = c + 1; c2 < min(c + D - 1, N); ++c2)
+                        mbar_wait(bar + (c2 & (D - 1)), (uint32_t)((c2 / D) & 1));
+                ok = false;
+                break;
+            }
+            const unsigned char* slot = slots + s * SB;
+            const T* col = reinterpret_cast<const T*>(slot + s_off[s][0]);
+            const int dp = (int)(*reinterpret_cast<const int32_t*>(slot + SB - 32 + s_off[s][1]) - c);
+            const T bent = *reinterpret_cast<const T*>(slot + SB - 16 + s_off[s][2]);
+            const int ps_ = cs + dp < W1 ? cs + dp : cs + dp - W1;
+            const T wc = win[cs];
+            const T yc = dp == 0 ? wc : win[ps_];
+            const int lim = (int)min(kl, N - 1 - c);
+            for (int t = tid; t <= KL; t += SOLVE_THREADS) {
+                int sl = cs + 1 + t;
+                if (sl >= W1) sl -= W1;
                 if (t < lim) {
-                    const int64_t i = j - 1 - t;
-                    win[i % W] -= pf[s * KU + t] * xj;
-                } else if (t == KU && j - 1 - KU >= 0) {
-                    win[(j - 1 - KU) % W] = pe[s];
+                    const T v = t + 1 == dp ? wc : win[sl];
+                    win[sl] = v - col[t] * yc;
+                } else if (t == KL && c + 1 + kl < N) {
+                    win[sl] = bent;   // the row entering the window
                 }
             }
             if (tid == 0) {
-                x[j] = xj;
-                if (!std::is_same<T, TV>::value) xo[j] = (TV)xj;
+                wy[c] = yc;
+                issue(c + D - 1);
             }
-            issue(j - (D - 1));
+            cs = cs + 1 == W1 ? 0 : cs + 1;
         }
-        cp_async_wait<0>();
     }
+    // all staged copies of the forward phase have landed or were never
+    // issued (columns >= N); its results y, written by thread 0, go to the
+    // bulk copies of the back phase
+    __syncthreads();
+    if (!ok) return;
+    if (tid == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    // ---- back: for j = N-1 .. 0: x_j = y_j / U_jj, rows j-1 .. j-KU -= U(., j) x_j
+    {
+        const int KUi = (int)KU;
+        for (int64_t i = (N - 1 - KU > 0 ? N - 1 - KU : 0) + tid; i < N; i += SOLVE_THREADS) win[i % W] = wy[i];
+        // the back phase continues the slots' phases: the forward phase used
+        // slot k for columns c = k, k + D, ... < N
+        auto uses = [&](int k) { return (N - 1 - k) >= 0 ? (N - 1 - k) / D + 1 : 0; };
+        auto issue = [&](int64_t j, int64_t step) {   // thread 0: stage column j (the step-th of this phase)
+            if (j < 0) return;
+            const int s = (int)(step & (D - 1));
+            unsigned char* slot = slots + s * SB;
+            const int lim = (int)min(KU, j);
+            const Span col = span_of(f.ab + j * ldab, (size_t)max(KUi, 1) * sizeof(T));
+            const Span ud = span_of(f.udiag + j, sizeof(T));
+            const bool enter = j - 1 - KU >= 0;
+            const Span ye = span_of(wy + (enter ? j - 1 - KU : j), sizeof(T));
+            (void)lim;
+            s_off[s][0] = col.off;
+            s_off[s][1] = ud.off;
+            s_off[s][2] = ye.off;
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_expect_tx(bar + s, col.bytes + ud.bytes + ye.bytes);
+            bulk_g2s(slot, col.src, col.bytes, bar + s);
+            bulk_g2s(slot + SB - 32, ud.src, ud.bytes, bar + s);
+            bulk_g2s(slot + SB - 16, ye.src, ye.bytes, bar + s);
+        };
+        __syncthreads();
+        if (tid == 0)
+            for (int64_t q = 0; q < D - 1; ++q) issue(N - 1 - q, q);
+        __syncthreads();
+        int js = (int)((N - 1) % W);   // ring slot of row j
+        for (int64_t q = 0; q < N; ++q) {
+            const int64_t j = N - 1 - q;
+            const int s = (int)(q & (D - 1));
+            if (!mbar_wait(bar + s, (uint32_t)((uses(s) + q / D) & 1))) {
+                s_err = 1;
+                atomicExch(a.err, 1);
+            }
+            __syncthreads();
+            if (s_err) {
+                if (tid == 0)
+                    for (int64_t q2 = q + 1; q2 < min(q + D - 1, N); ++q2)
+                        mbar_wait(bar + (q2 & (D - 1)), (uint32_t)((uses((int)(q2 & (D - 1))) + q2 / D) & 1));
+                break;
+            }
+            const unsigned char* slot = slots + s * SB;
+            // U(j - KU .. j - 1, j) staged in increasing row order: row j - 1 - t at KU - 1 - t
+            const T* col = reinterpret_cast<const T*>(slot + s_off[s][0]);
+            const T ujj = *reinterpret_cast<const T*>(slot + SB - 32 + s_off[s][1]);
+            const T yent = *reinterpret_cast<const T*>(slot + SB - 16 + s_off[s][2]);
+            const T xj = win[js] / ujj;
+            const int lim = (int)min(KU, j);
+            for (int t = tid; t <= KUi; t += SOLVE_THREADS) {
+                int sl = js - 1 - t;
+                if (sl < 0) sl += W;
+                if (t < lim) {
+                    win[sl] -= col[KUi - 1 - t] * xj;
+                } else if (t == KUi && j - 1 - KU >= 0) {
+                    win[sl] = yent;
+                }
+            }
+            if (tid == 0) {
+                xo[j] = (TV)xj;
+                issue(j - (D - 1), q + D - 1);
+            }
+            js = js == 0 ? W - 1 : js - 1;
+        }
+    }
+    __syncthreads();
 }
 
 template <typename T>
 size_t solve_smem(int64_t kl, int64_t ku, int D) {
     const int64_t KU = kl + ku;
-    return (size_t)(KU + 2 + (int64_t)D * KU + 2 * D) * sizeof(T) + (size_t)D * (sizeof(double) + sizeof(int32_t)) + 8;
+    return (((size_t)(KU + 2) * sizeof(T) + 15) & ~(size_t)15) + (size_t)D * slot_bytes<T>(KU) +
+           (size_t)D * sizeof(uint64_t);
 }
 
-// the deepest prefetch ring (8 or 4 columns) whose shared memory fits; 0
-// when none does
+// the deepest staging ring (8 or 4 slots) whose shared memory fits; 0 when
+// none does
 template <typename T>
 int solve_depth(int64_t kl, int64_t ku) {
-    if (solve_smem<T>(kl, ku, 8) <= 227 * 1024) return 8;
-    if (solve_smem<T>(kl, ku, 4) <= 227 * 1024) return 4;
+    if (solve_smem<T>(kl, ku, 8) <= 220 * 1024) return 8;
+    if (solve_smem<T>(kl, ku, 4) <= 220 * 1024) return 4;
     return 0;
 }
 
@@ -483,10 +619,16 @@ rbffd_status lu_factor(const rbffd_op* op, double alpha, double beta, int dtype,
     lu->dtype = dtype;
     lu->alpha = alpha;
     lu->beta = beta;
-    cudaError_t e = cudaMalloc(&lu->ab, (size_t)lu->ldab * lu->N * elem);
-    if (e == cudaSuccess) e = cudaMalloc(&lu->lmul, (size_t)std::max<int64_t>(kl, 1) * lu->N * elem);
-    if (e == cudaSuccess) e = cudaMalloc(&lu->udiag, (size_t)lu->N * elem);
-    if (e == cudaSuccess) e = cudaMalloc(&lu->piv, (size_t)lu->N * sizeof(int32_t));
+    // every array the substitutions read by bulk copies is padded by 64
+    // bytes: a copy's 16-byte-aligned span may reach past the last element
+    const size_t pad = 64;
+    cudaError_t e = cudaMalloc(&lu->ab, (size_t)lu->ldab * lu->N * elem + pad);
+    if (e == cudaSuccess) e = cudaMalloc(&lu->lmul, (size_t)std::max<int64_t>(kl, 1) * lu->N * elem + pad);
+    if (e == cudaSuccess) e = cudaMalloc(&lu->udiag, (size_t)lu->N * elem + pad);
+    if (e == cudaSuccess) e = cudaMalloc(&lu->piv, (size_t)lu->N * sizeof(int32_t) + pad);
+    if (e == cudaSuccess) e = cudaMalloc(&lu->work, (size_t)(2 * lu->N + 16) * elem + pad);
+    if (e == cudaSuccess) e = cudaMalloc(&lu->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(lu->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         set_error("banded LU: %s (%lld x %lld band)", cudaGetErrorString(e), (long long)lu->ldab, (long long)lu->N);
@@ -505,7 +647,7 @@ rbffd_status lu_factor(const rbffd_op* op, double alpha, double beta, int dtype,
 namespace {
 template <typename T, typename TV>
 rbffd_status solve_step_t(rbffd_lu* const (&fac)[4][2], const rbffd_lu* any, int nspecies, const void* const b[2],
-                          void* const x[2], const int* ord_flag, void* ywork, cudaStream_t st) {
+                          void* const x[2], const int* ord_flag, void* work, int* err, cudaStream_t st) {
     SolveArgs<T, TV> a;
     memset(&a, 0, sizeof(a));
     for (int k = 0; k < 4; ++k)
@@ -519,22 +661,22 @@ rbffd_status solve_step_t(rbffd_lu* const (&fac)[4][2], const rbffd_lu* any, int
     a.ku = any->ku;
     a.ldab = any->ldab;
     a.ord_flag = ord_flag;
-    a.ywork = (T*)ywork;
+    a.work = (T*)work;
+    a.err = err;
     return launch_solve(a, nspecies, st);
 }
 }  // namespace
 
 rbffd_status lu_solve_step(rbffd_lu* const (&fac)[4][2], int nspecies, const void* const b[2], void* const x[2],
-                           int vec_dtype, const int* ord_flag, void* ywork, cudaStream_t st) {
+                           int vec_dtype, const int* ord_flag, void* work, int* err, cudaStream_t st) {
     const rbffd_lu* any = nullptr;
     for (int k = 0; k < 4 && !any; ++k) any = fac[k][0];
-    RBFFD_CHECK_ARG(any, "no LU factor");
+    RBFFD_CHECK_ARG(any && work && err, "no LU factor / work vector / error flag");
     const bool f32 = any->dtype == RBFFD_F32, v32 = vec_dtype == RBFFD_F32;
-    RBFFD_CHECK_ARG(f32 == v32 || ywork, "mixed-precision substitutions need a work vector");
-    if (f32 && v32) return solve_step_t<float, float>(fac, any, nspecies, b, x, ord_flag, ywork, st);
-    if (!f32 && !v32) return solve_step_t<double, double>(fac, any, nspecies, b, x, ord_flag, ywork, st);
-    if (!f32 && v32) return solve_step_t<double, float>(fac, any, nspecies, b, x, ord_flag, ywork, st);
-    return solve_step_t<float, double>(fac, any, nspecies, b, x, ord_flag, ywork, st);
+    if (f32 && v32) return solve_step_t<float, float>(fac, any, nspecies, b, x, ord_flag, work, err, st);
+    if (!f32 && !v32) return solve_step_t<double, double>(fac, any, nspecies, b, x, ord_flag, work, err, st);
+    if (!f32 && v32) return solve_step_t<double, float>(fac, any, nspecies, b, x, ord_flag, work, err, st);
+    return solve_step_t<float, double>(fac, any, nspecies, b, x, ord_flag, work, err, st);
 }
 
 }  // namespace rbffd
@@ -564,7 +706,17 @@ rbffd_status rbffd_lu_solve(const rbffd_lu* lu, const void* b, void* x, void* st
     fac[0][0] = const_cast<rbffd_lu*>(lu);
     const void* bb[2] = {b, nullptr};
     void* xx[2] = {x, nullptr};
-    return lu_solve_step(fac, 1, bb, xx, lu->dtype, nullptr, nullptr, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    rbffd_status s = lu_solve_step(fac, 1, bb, xx, lu->dtype, nullptr, lu->work, lu->err, st);
+    if (s != RBFFD_OK) return s;
+    int h = 0;
+    RBFFD_CUDA_TRY(cudaMemcpyAsync(&h, lu->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("banded LU solve: a bounded wait for staged factor columns gave up");
+        return RBFFD_TIMEOUT;
+    }
+    return RBFFD_OK;
 }
 
 int64_t rbffd_lu_bytes(const rbffd_lu* lu) {

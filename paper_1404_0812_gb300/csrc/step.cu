@@ -45,7 +45,7 @@ struct rbffd_step_ws {
     int solver;                       // solver the graph was captured with
     rbffd_lu* lu[4][2];               // banded LU factors by SBDF order and species
     rbffd_lu* graph_lu[4][2];         // the factors the captured graph's solve reads
-    double* ywork;                    // 2 N float64: the LU substitutions' forward results
+    double* ywork;                    // the LU substitutions' work: per species 2 N + 16 float64
 };
 
 namespace rbffd {
@@ -602,7 +602,7 @@ rbffd_status launch_step(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
         const void* b[2] = {V(a, 0, VB), a.ns == 2 ? V(a, 1, VB) : nullptr};
         void* x[2] = {a.u, a.ns == 2 ? a.v : nullptr};
         rbffd_status r = lu_solve_step(ws->lu, a.ns, b, x, std::is_same<T, float>::value ? RBFFD_F32 : RBFFD_F64,
-                                       ws->flags + 4, ws->ywork, st);
+                                       ws->flags + 4, ws->ywork, ws->flags, st);
         if (r != RBFFD_OK) return r;
     }
     return RBFFD_OK;
@@ -755,7 +755,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
                 }
             }
         }
-        if (!ws->ywork) RBFFD_CUDA_TRY(cudaMalloc(&ws->ywork, 2 * op->N * sizeof(double)));
+        if (!ws->ywork) RBFFD_CUDA_TRY(cudaMalloc(&ws->ywork, (2 * (2 * op->N + 16)) * sizeof(double) + 64));
     }
     RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, st));
     RBFFD_CUDA_TRY(cudaMemcpyAsync(ws->tstart, &s->t, sizeof(double), cudaMemcpyHostToDevice, st));
