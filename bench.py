@@ -76,8 +76,8 @@ def _parse():
     ap.add_argument("--profile-n", type=int, default=40_000, help="nodes of the --profile case")
     ap.add_argument("--profile-plain", action="store_true", help="--profile without the learned start")
     ap.add_argument("--horizons", action="store_true",
-                    help="the long-horizon stepping studies only (C2 5000 steps, the 2M-node Gray-Scott "
-                         "stand-in 10k steps in float32 and float64); one JSON line")
+                    help="the long-horizon stepping studies only (C2 5000 steps, the 2M-node unit-sphere "
+                         "Gray-Scott stand-in 10k steps in float32 and float64); one JSON line")
     return ap.parse_args()
 
 
@@ -273,7 +273,8 @@ def configs_report(R, W, T, torch, nets):
     out = {}
     for name, fn in (("sphere2562_heat", _c1), ("torus40k_schnakenberg", _c2),
                      ("torus40k_direct_lu_vs_bicgstab", _c2_lu), ("bumpy500k_learned", _c4),
-                     ("bumpy2m_pointcloud", _c5), ("bumpy2m_analytic_gray_scott", _c5_standin),
+                     ("bumpy2m_pointcloud", _c5), ("bumpy2m_analytic_gray_scott", _c5_bumpy),
+                     ("sphere2m_gray_scott", _c5_standin),
                      ("reorder_1m_shuffled", _reorder),
                      ("sphere_heat_convergence_bdf4", _e3),
                      ("forced_sphere_convergence_bdf4", _e4), ("forced_torus_convergence_bdf4", _e5),
@@ -672,22 +673,27 @@ def _c5(R, W, T, torch, nets):
     return out
 
 
-def _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=None):
-    """The largest stable stand-in of the point-cloud configuration: the
-    bumpy sphere at N = 2,000,000 with analytic normals and no jitter (the
-    jittered PCA-normal cloud has eigenvalues of L_X far in the right
-    half-plane, see test_pointcloud_spectrum), n = 70, learned build;
-    Gray-Scott in float32 for `steps` steps (ms per step), float64 beside it
-    for the parity window (100 steps) and, with f64_steps, up to that
-    horizon for the full-horizon difference."""
-    ns = W.bumpy_sphere(2_000_000, jitter=0.0, seed=4, normals="analytic")
+def _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=None, surface="sphere"):
+    """Stand-ins of the 2M-node point-cloud Gray-Scott run (whose jittered,
+    PCA-normal operator has eigenvalues far in the right half-plane, see
+    test_pointcloud_spectrum): surface "bumpy" = the same bumpy sphere with
+    analytic normals and no jitter (its conical poles still leave a positive
+    part: reported, with the step at which BiCGSTAB fails), "sphere" = the
+    unit sphere at N = 2,000,000 (Fibonacci nodes, exact normals: spectrum
+    in the closed left half-plane), both n = 70, learned build.  Gray-Scott
+    in float32 for `steps` steps (ms per step), float64 beside it for the
+    parity window (100 steps) and, with f64_steps, to that horizon for the
+    full-horizon difference.  A run stops at its first solver failure."""
+    ns = (W.bumpy_sphere(2_000_000, jitter=0.0, seed=4, normals="analytic") if surface == "bumpy"
+          else W.fibonacci_sphere(2_000_000))
     op = R.build_operator(T(ns.X), T(ns.normals), 70, kernel="imq", kappa_target=KAPPA_T,
                           mlps=[nets[SIZES.index(70)]], allow_failures=True)
     info = R.get_stencil_info(op)
     g = W.GRAY_SCOTT
     name, coef = R.model_coefs(g)
     u0, v0 = W.gray_scott_initial(ns.X, seed=5, spots=50, radius=0.05)
-    out = {"stencils_ok_fraction": round(float(((info["status"] == 0) | (info["status"] == 4)).double().mean()), 6),
+    out = {"surface": surface, "N": ns.N, "n": 70,
+           "stencils_ok_fraction": round(float(((info["status"] == 0) | (info["status"] == 4)).double().mean()), 6),
            "build_ms": round(sum(R.get_build_timings(op).values()), 1)}
     st, p = {}, {}
     for dt_, tol in ((torch.float32, 1e-6), (torch.float64, 1e-12)):
@@ -697,8 +703,8 @@ def _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=None):
     diffs = {}
     done = {torch.float32: 0, torch.float64: 0}
     ms32 = 0.0
-    marks = [100] + ([f64_steps] if f64_steps else [])
-    for upto in marks:
+    failed = False
+    for upto in [100] + ([f64_steps] if f64_steps else []):
         for dt_ in (torch.float32, torch.float64):
             a, b = _ev(torch)
             a.record()
@@ -709,25 +715,34 @@ def _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=None):
                 ms32 += a.elapsed_time(b)
             done[dt_] = upto
             if rep["status"] != 0:
-                out[f"solver_failure_{'f32' if dt_ == torch.float32 else 'f64'}"] = rep
+                out[f"solver_failure_{'f32' if dt_ == torch.float32 else 'f64'}"] = {
+                    k: rep[k] for k in ("failed_step", "max_iters_u", "max_iters_v")}
+                failed = True
         diffs[upto] = max(float((getattr(st[torch.float32], k).double() - getattr(st[torch.float64], k)).abs().max()
                                 / getattr(st[torch.float64], k).abs().max()) for k in ("u", "v"))
-    if steps > done[torch.float32]:
+        if failed:
+            break
+    if not failed and steps > done[torch.float32]:
         a, b = _ev(torch)
         a.record()
         rep = R.step_imex(op, st[torch.float32], p[torch.float32], steps - done[torch.float32], allow_failure=True)
         b.record()
         torch.cuda.synchronize()
         ms32 += a.elapsed_time(b)
+        done[torch.float32] = steps
         if rep["status"] != 0:
-            out["solver_failure_f32"] = rep
+            out["solver_failure_f32"] = {k: rep[k] for k in ("failed_step", "max_iters_u", "max_iters_v")}
     out["f32_vs_f64_rel_linf"] = {str(k): v for k, v in diffs.items()}
-    out["steps_f32"] = steps
-    out["ms_per_step_f32"] = round(ms32 / steps, 4)
-    u = st[torch.float32].u
-    out["u_range_f32_end"] = [float(u.min()), float(u.max())]
-    out["finite_f32_end"] = bool(torch.isfinite(u).all().item())
+    out["steps_f32"] = done[torch.float32]
+    out["ms_per_step_f32"] = round(ms32 / max(done[torch.float32], 1), 4)
+    for k in ("u", "v"):
+        x = getattr(st[torch.float32], k)
+        out[f"{k}_range_f32_end"] = [float(x.min()), float(x.max())]
     return out
+
+
+def _c5_bumpy(R, W, T, torch, nets):
+    return _c5_standin(R, W, T, torch, nets, steps=100, surface="bumpy")
 
 
 def run_ours(args):
@@ -778,7 +793,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         out = {"horizons": True,
                "torus40k_schnakenberg": _c2(R, W, T, torch, nets),
-               "bumpy2m_analytic_gray_scott": _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=10_000)}
+               "sphere2m_gray_scott": _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=10_000)}
         out["wall_s"] = round(time.perf_counter() - t0, 1)
         print(json.dumps(out))
         return

@@ -183,24 +183,64 @@ __device__ __forceinline__ void load4(const double* p, double (&w)[4]) {
 // (L x0)_row and (L x1)_row in one pass over the row (x read L1-bypassing:
 // within one launch L1 is not coherent across SMs); software-pipelined so
 // that a chunk's index and weight loads overlap the previous chunk's gathers
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <typename T>
-__device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, const T* x0, const T* x1, bool two,
-                                       T& y0, T& y1) {
+__device__ __forceinline__ int4 ld_stream4(const int32_t* p) { return __ldcs(reinterpret_cast<const int4*>(p)); }
+__device__ __forceinline__ void load4s(const float* p, float (&w)[4]) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+__device__ __forceinline__ void load4s(const double* p, double (&w)[4]) {
+    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2*>(p + 2));
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+
+constexpr int PF_CHUNKS = 6;   // ELL chunks prefetched into L2 ahead of use
+
+// (L x0)_row and (L x1)_row in one pass over the row (x read L1-bypassing:
+// within one launch L1 is not coherent across SMs); software-pipelined so
+// that a chunk's index and weight loads overlap the previous chunk's
+// gathers, with an L2 prefetch PF_CHUNKS chunks ahead that runs on into the
+// thread's next row (rnext), and streaming (evict-first) loads of the
+// single-use ELL so that the Krylov vectors stay in L2
+template <typename T>
+__device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, int64_t rnext, const T* x0, const T* x1,
+                                       bool two, T& y0, T& y1) {
     int g = group_of_row(a.gi, r);
-    const int npad = a.gi.npad[g];
+    const int npad = a.gi.npad[g], nch = npad >> 2;
     const int64_t base = ell_elem(a.gi.ell_off[g], npad, r - a.gi.row_begin[g], 0);
+    int64_t nbase = -1;
+    int nnch = 0;
+    if (rnext < a.N) {
+        const int gn = group_of_row(a.gi, rnext);
+        nnch = a.gi.npad[gn] >> 2;
+        nbase = ell_elem(a.gi.ell_off[gn], a.gi.npad[gn], rnext - a.gi.row_begin[gn], 0);
+    }
     T s0 = T(0), s1 = T(0);
-    int4 iv = __ldg(reinterpret_cast<const int4*>(a.idx + base));
+    int4 iv = __ldcs(reinterpret_cast<const int4*>(a.idx + base));
     T wv[4];
-    load4(a.w + base, wv);
-    for (int jb = 0; jb < npad; jb += 4) {
+    load4s(a.w + base, wv);
+    for (int c = 0; c < nch; ++c) {
+        // L2 prefetch PF_CHUNKS ahead (into the next row past this one's end)
+        {
+            const int k = c + PF_CHUNKS;
+            int64_t e = -1;
+            if (k < nch) e = base + (int64_t)k * 128;
+            else if (k - nch < nnch && nbase >= 0) e = nbase + (int64_t)(k - nch) * 128;
+            if (e >= 0) {
+                prefetch_l2(a.idx + e);
+                prefetch_l2(a.w + e);
+            }
+        }
         // the next chunk's index and weight loads go out before this chunk's gathers
         int4 ivn = iv;
         T wn[4] = {wv[0], wv[1], wv[2], wv[3]};
-        if (jb + 4 < npad) {
-            const int64_t en = base + (int64_t)((jb + 4) >> 2) * 128;
-            ivn = __ldg(reinterpret_cast<const int4*>(a.idx + en));
-            load4(a.w + en, wn);
+        if (c + 1 < nch) {
+            const int64_t en = base + (int64_t)(c + 1) * 128;
+            ivn = __ldcs(reinterpret_cast<const int4*>(a.idx + en));
+            load4s(a.w + en, wn);
         }
         const int ii[4] = {iv.x, iv.y, iv.z, iv.w};
         T g0[4], g1[4];
@@ -252,7 +292,7 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
         for (int64_t r = t0; r < a.N; r += stride) {
             int i = a.row_node[r];
             T Lu, Lv;
-            row_L2(a, r, u, v, two, Lu, Lv);
+            row_L2(a, r, r + stride, u, v, two, Lu, Lv);
             T ui = u[i], vi = two ? v[i] : T(0);
             T f, g;
             react(a, ui, vi, f, g);
@@ -382,7 +422,7 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
             for (int64_t r = t0; r < a.N; r += stride) {
                 int i = a.row_node[r];
                 T L0, L1;
-                row_L2(a, r, V(a, 0, VP), two ? V(a, 1, VP) : nullptr, two && active[1], L0, L1);
+                row_L2(a, r, r + stride, V(a, 0, VP), two ? V(a, 1, VP) : nullptr, two && active[1], L0, L1);
                 if (active[0]) {
                     T q = c0 * V(a, 0, VP)[i] - k0 * L0;
                     V(a, 0, VQ)[i] = q;
@@ -445,7 +485,7 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
                 int i = a.row_node[r];
                 T L0 = T(0), L1 = T(0);
                 if (need0 || need1)
-                    row_L2(a, r, V(a, 0, VS), two ? V(a, 1, VS) : nullptr, two && need1, L0, L1);
+                    row_L2(a, r, r + stride, V(a, 0, VS), two ? V(a, 1, VS) : nullptr, two && need1, L0, L1);
                 for (int k = 0; k < 2; ++k) {
                     T* x = k == 0 ? u : v;
                     if (early[k]) {

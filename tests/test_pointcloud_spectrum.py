@@ -11,8 +11,12 @@ the right half-plane (max Re ~ +5.8e5) than into the left (min Re ~ -2.6e5),
 while the same surface sampled without jitter and with analytic normals has
 a positive part some 600 times smaller (max Re ~ +960 against min Re
 ~ -1600; the conical points of r = 1 + 0.1 sin 3theta cos 4phi at the poles
-leave it a little).  The implicit Gray-Scott system (I - dt delta L) of the point cloud
-is therefore not the stable one BiCGSTAB is meant for."""
+leave it a little) -- enough to make Gray-Scott stepping blow up at 2M nodes
+as well -- and the smooth unit sphere (Fibonacci nodes, exact normals) has
+its spectrum in the closed left half-plane (max Re at rounding level, the
+constant mode), which is why it is the stable stand-in of the 2M-node
+Gray-Scott run.  The implicit Gray-Scott system (I - dt delta L) of the
+point cloud is therefore not the stable one BiCGSTAB is meant for."""
 import numpy as np
 
 from oracle import operator as oop
@@ -40,3 +44,6 @@ def test_pointcloud_spectrum_right_half_plane():
     assert ls.real.max() < abs(ls.real.min())
     assert lc.real.max() > 100 * max(ls.real.max(), 1.0)
     assert scale_c > scale_s
+    sphere = _spectrum(W.fibonacci_sphere(N))
+    print(f"unit sphere: max Re {sphere.real.max():.4g}, min Re {sphere.real.min():.4g}")
+    assert sphere.real.max() < 1e-8 * abs(sphere.real.min())
