@@ -17,12 +17,38 @@
 // read with L1-bypassing loads.  The solution is updated in place in u
 // (after the right-hand side is formed, u is only read by its own row).
 // The launch can be captured once into a CUDA graph and replayed per step.
+//
+// Large operators take a second path with the same arithmetic per row:
+// BiCGSTAB as a sequence of full-occupancy phase kernels under a device-side
+// WHILE graph node (the phase-kernel section below says why and how).
 #include "common.cuh"
 
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
+
+// Loop state of the phase-kernel BiCGSTAB (device memory).  Each phase
+// kernel reads it as its previous kernel left it; only the last block of a
+// phase (by ticket) writes it, after every other block of that phase has
+// finished reading.
+struct PhaseCtl {
+    double totR[6];              // phase R: |b|^2, |r0|^2 (u: 0, 1; v: 3, 4)
+    double totB[2];              // (r-hat, q)
+    double totC[2];              // |s|^2
+    double totD[4];              // (t, s), (t, t) per species
+    double totE[4];              // (r-hat, r), |r|^2 per species
+    double bnorm[2], rho[2], rho_prev[2], alpha[2], omega[2], relres[2];
+    int active[2], conv[2], fail[2], iters[2], zero[2];
+    // the current iteration's scalars and decisions, each set once by the
+    // last block of the phase that makes it (the phase kernels' threads only
+    // read them: no per-thread float64 scalar arithmetic)
+    double beta[2], alpha_n[2], omega_n[2];
+    int actA[2], actB[2], early[2], actE[2];
+    int it;                      // iterations done in this step
+    int more;                    // the loop continues (host-loop mode reads it)
+    unsigned int ticket;
+};
 
 struct rbffd_step_ws {
     int dtype;
@@ -42,10 +68,13 @@ struct rbffd_step_ws {
     cudaStream_t cap;                 // library-owned stream used only for capture
     unsigned char graph_args[1024];   // kernel arguments the graph holds
     size_t graph_args_size;
-    int solver;                       // solver the graph was captured with
+    int solver;                       // path the graph was captured with (0 cooperative, 1 LU, 2 phases)
     rbffd_lu* lu[4][2];               // banded LU factors by SBDF order and species
     rbffd_lu* graph_lu[4][2];         // the factors the captured graph's solve reads
     double* ywork;                    // the LU substitutions' work: per species 2 N + 16 float64
+    PhaseCtl* ctl;                    // phase-kernel path: loop state
+    double* pp;                       //   per-block partial sums
+    int phased;                       // 1: BiCGSTAB as phase kernels (large operators)
 };
 
 namespace rbffd {
@@ -64,6 +93,8 @@ void step_ws_free(rbffd_step_ws* ws) {
     for (auto& row : ws->lu)
         for (rbffd_lu* f : row) lu_free(f);
     cudaFree(ws->ywork);
+    cudaFree(ws->ctl);
+    cudaFree(ws->pp);
     delete ws;
 }
 
@@ -100,6 +131,9 @@ struct Args {
     int* rep;
     double* rep_res;
     int rhs_only;      // 1: form the right-hand side b only (a direct solve follows)
+    PhaseCtl* ctl;                         // phase-kernel path: loop state and totals
+    double* pp;                            //   per-block partial sums (blocks x 8)
+    cudaGraphConditionalHandle cond;       //   WHILE handle of the step graph (0: host loop)
 };
 
 enum { VB = 0, VR = 1, VRH = 2, VP = 3, VQ = 4, VS = 5, VT = 6 };
@@ -168,16 +202,6 @@ __device__ __forceinline__ void react(const Args<T>& a, T u, T v, T& f, T& g) {
         } break;
         default: f = T(0); g = T(0);
     }
-}
-
-__device__ __forceinline__ void load4(const float* p, float (&w)[4]) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-}
-__device__ __forceinline__ void load4(const double* p, double (&w)[4]) {
-    double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
 }
 
 // (L x0)_row and (L x1)_row in one pass over the row (x read L1-bypassing:
@@ -262,6 +286,151 @@ __device__ __forceinline__ void row_L2(const Args<T>& a, int64_t r, int64_t rnex
     y1 = two ? s1 : T(0);
 }
 
+// the SBDF order, report slot and coefficients of the current step (from
+// the flags a previous launch left; the same in every block)
+template <typename T>
+struct StepCoef {
+    int nhist, ord, slot;
+    T c0, cl, k0, k1, samp;
+};
+
+template <typename T>
+__device__ __forceinline__ StepCoef<T> step_coef(const Args<T>& a) {
+    StepCoef<T> k;
+    // past levels available -> the order of this step (SBDF1 .. SBDF4, the
+    // first steps of a run without history climb one order per step)
+    k.nhist = *((volatile int*)(a.flags + 2));
+    k.ord = min(a.order, k.nhist + 1);
+    k.slot = *((volatile int*)(a.flags + 3));
+    // the SBDFk system scaled to integer coefficients:
+    //   c0 u^{n+1} - cl delta L u^{n+1} = sum_j A_j u^{n-j} + cl sum_j B_j f^{n-j}
+    // k = 1: c0 1, cl dt;  k = 2: 3, 2 dt;  k = 3: 11, 6 dt;  k = 4: 25, 12 dt
+    const int ord = k.ord;
+    k.c0 = ord == 1 ? T(1) : ord == 2 ? T(3) : ord == 3 ? T(11) : T(25);
+    k.cl = (ord == 1 ? T(1) : ord == 2 ? T(2) : ord == 3 ? T(6) : T(12)) * a.dt;
+    k.k0 = k.cl * a.delta[0];
+    k.k1 = k.cl * a.delta[1];
+    // the source is taken at the new time level t^{n+1} (implicitly)
+    k.samp = (a.su || a.sv) ? (T)exp(a.src_rate * (*a.tstart + (double)(k.slot + 1) * (double)a.dt)) : T(0);
+    return k;
+}
+
+// Dot-product accumulators.  The cooperative kernel sums in float64 (the
+// float32 products are exact there).  The phase kernels sum float32 products
+// with the compensated dot product Dot2 (Ogita, Rump & Oishi, "Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26 (2005), Algorithm 5.3): each
+// product a b split exactly into p + e by an FMA (TwoProduct), the running
+// sum carried by Knuth's error-free TwoSum, the rounding errors of both
+// summed apart and added at the end.  The result is as accurate as the sum
+// computed in twice the working precision, with float32 instructions only
+// (the float64 pipe of this GPU is a small fraction of the float32 one).
+struct Dot2 {
+    float hi, lo;
+};
+__device__ __forceinline__ void acc_zero(Dot2& s) { s.hi = s.lo = 0.f; }
+__device__ __forceinline__ void acc_zero(double& s) { s = 0.0; }
+__device__ __forceinline__ void acc_add(Dot2& s, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);                    // a b = p + e exactly
+    const float x = __fadd_rn(s.hi, p);
+    const float z = __fsub_rn(x, s.hi);
+    const float t = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(x, z)), __fsub_rn(p, z));   // s.hi + p = x + t exactly
+    s.hi = x;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(t, e));
+}
+__device__ __forceinline__ void acc_add(double& s, float a, float b) { s += (double)a * b; }
+__device__ __forceinline__ void acc_add(double& s, double a, double b) { s += a * b; }
+__device__ __forceinline__ double acc_value(const Dot2& s) { return (double)s.hi + (double)s.lo; }
+__device__ __forceinline__ double acc_value(double s) { return s; }
+
+// the phase kernels' accumulator for state type T
+template <typename T>
+struct PhaseAcc {
+    using type = double;
+};
+template <>
+struct PhaseAcc<float> {
+    using type = Dot2;
+};
+
+// phase R of one row (node i, with (L u)_i = Lu, (L v)_i = Lv): kinetics,
+// right-hand side b of the step's SBDF order, history rotation, r0 = b - A u,
+// r-hat = r0, p = q = 0; accumulates |b|^2, |r0|^2 per species into d[0..1],
+// d[3..4]
+template <typename T, typename A>
+__device__ __forceinline__ void rhs_row(const Args<T>& a, const StepCoef<T>& kc, int64_t i, T Lu, T Lv,
+                                        A (&d)[6]) {
+    const bool two = a.ns == 2;
+    const int ord = kc.ord;
+    const T c0 = kc.c0, cl = kc.cl, k0 = kc.k0, k1 = kc.k1, samp = kc.samp;
+    T* u = a.u;
+    T* v = two ? a.v : nullptr;
+    T ui = u[i], vi = two ? v[i] : T(0);
+    T f, g;
+    react(a, ui, vi, f, g);
+    T bu, bv = T(0);
+    if (ord == 2) {
+        bu = T(4) * ui - a.up[i] + T(2) * a.dt * (T(2) * f - a.fp[i]);
+        if (two) bv = T(4) * vi - a.vp[i] + T(2) * a.dt * (T(2) * g - a.gp[i]);
+    } else if (ord == 1) {
+        bu = ui + a.dt * f;
+        if (two) bv = vi + a.dt * g;
+    } else if (ord == 3) {
+        bu = (T(18) * ui - T(9) * a.up[i] + T(2) * a.up2[i]) +
+             cl * (T(3) * f - T(3) * a.fp[i] + a.fp2[i]);
+        if (two)
+            bv = (T(18) * vi - T(9) * a.vp[i] + T(2) * a.vp2[i]) +
+                 cl * (T(3) * g - T(3) * a.gp[i] + a.gp2[i]);
+    } else {
+        bu = (T(48) * ui - T(36) * a.up[i] + T(16) * a.up2[i] - T(3) * a.up3[i]) +
+             cl * (T(4) * f - T(6) * a.fp[i] + T(4) * a.fp2[i] - a.fp3[i]);
+        if (two)
+            bv = (T(48) * vi - T(36) * a.vp[i] + T(16) * a.vp2[i] - T(3) * a.vp3[i]) +
+                 cl * (T(4) * g - T(6) * a.gp[i] + T(4) * a.gp2[i] - a.gp3[i]);
+    }
+    if (a.su) bu += cl * samp * a.su[i];
+    if (two && a.sv) bv += cl * samp * a.sv[i];
+    // shift the history by one level (only the levels the order keeps)
+    if (a.order >= 4) {
+        a.up3[i] = a.up2[i];
+        a.fp3[i] = a.fp2[i];
+    }
+    if (a.order >= 3) {
+        a.up2[i] = a.up[i];
+        a.fp2[i] = a.fp[i];
+    }
+    a.up[i] = ui;
+    a.fp[i] = f;
+    T ru = bu - (c0 * ui - k0 * Lu);
+    V(a, 0, VB)[i] = bu;
+    V(a, 0, VR)[i] = ru;
+    V(a, 0, VRH)[i] = ru;
+    V(a, 0, VP)[i] = T(0);
+    V(a, 0, VQ)[i] = T(0);
+    acc_add(d[0], bu, bu);
+    acc_add(d[1], ru, ru);
+    if (two) {
+        if (a.order >= 4) {
+            a.vp3[i] = a.vp2[i];
+            a.gp3[i] = a.gp2[i];
+        }
+        if (a.order >= 3) {
+            a.vp2[i] = a.vp[i];
+            a.gp2[i] = a.gp[i];
+        }
+        a.vp[i] = vi;
+        a.gp[i] = g;
+        T rv = bv - (c0 * vi - k1 * Lv);
+        V(a, 1, VB)[i] = bv;
+        V(a, 1, VR)[i] = rv;
+        V(a, 1, VRH)[i] = rv;
+        V(a, 1, VP)[i] = T(0);
+        V(a, 1, VQ)[i] = T(0);
+        acc_add(d[3], bv, bv);
+        acc_add(d[4], rv, rv);
+    }
+}
+
 // NT threads per block: 1024 (one block per SM, <= 64 registers) for large
 // operators, 256 for small ones
 template <typename T, int NT>
@@ -269,20 +438,10 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool two = a.ns == 2;
-    // past levels available -> the order of this step (SBDF1 .. SBDF4, the
-    // first steps of a run without history climb one order per step)
-    const int nhist = *((volatile int*)(a.flags + 2));
-    const int ord = min(a.order, nhist + 1);
-    const int slot = *((volatile int*)(a.flags + 3));
+    const StepCoef<T> kc = step_coef(a);
+    const int nhist = kc.nhist, ord = kc.ord, slot = kc.slot;
+    const T c0 = kc.c0, k0 = kc.k0, k1 = kc.k1;
     unsigned long long target = 0;
-    // the SBDFk system scaled to integer coefficients:
-    //   c0 u^{n+1} - cl delta L u^{n+1} = sum_j A_j u^{n-j} + cl sum_j B_j f^{n-j}
-    // k = 1: c0 1, cl dt;  k = 2: 3, 2 dt;  k = 3: 11, 6 dt;  k = 4: 25, 12 dt
-    const T c0 = ord == 1 ? T(1) : ord == 2 ? T(3) : ord == 3 ? T(11) : T(25);
-    const T cl = (ord == 1 ? T(1) : ord == 2 ? T(2) : ord == 3 ? T(6) : T(12)) * a.dt;
-    const T k0 = cl * a.delta[0], k1 = cl * a.delta[1];
-    // the source is taken at the new time level t^{n+1} (implicitly)
-    const T samp = (a.su || a.sv) ? (T)exp(a.src_rate * (*a.tstart + (double)(slot + 1) * (double)a.dt)) : T(0);
     T* u = a.u;
     T* v = two ? a.v : nullptr;
 
@@ -293,70 +452,7 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
             int i = a.row_node[r];
             T Lu, Lv;
             row_L2(a, r, r + stride, u, v, two, Lu, Lv);
-            T ui = u[i], vi = two ? v[i] : T(0);
-            T f, g;
-            react(a, ui, vi, f, g);
-            T bu, bv = T(0);
-            if (ord == 2) {
-                bu = T(4) * ui - a.up[i] + T(2) * a.dt * (T(2) * f - a.fp[i]);
-                if (two) bv = T(4) * vi - a.vp[i] + T(2) * a.dt * (T(2) * g - a.gp[i]);
-            } else if (ord == 1) {
-                bu = ui + a.dt * f;
-                if (two) bv = vi + a.dt * g;
-            } else if (ord == 3) {
-                bu = (T(18) * ui - T(9) * a.up[i] + T(2) * a.up2[i]) +
-                     cl * (T(3) * f - T(3) * a.fp[i] + a.fp2[i]);
-                if (two)
-                    bv = (T(18) * vi - T(9) * a.vp[i] + T(2) * a.vp2[i]) +
-                         cl * (T(3) * g - T(3) * a.gp[i] + a.gp2[i]);
-            } else {
-                bu = (T(48) * ui - T(36) * a.up[i] + T(16) * a.up2[i] - T(3) * a.up3[i]) +
-                     cl * (T(4) * f - T(6) * a.fp[i] + T(4) * a.fp2[i] - a.fp3[i]);
-                if (two)
-                    bv = (T(48) * vi - T(36) * a.vp[i] + T(16) * a.vp2[i] - T(3) * a.vp3[i]) +
-                         cl * (T(4) * g - T(6) * a.gp[i] + T(4) * a.gp2[i] - a.gp3[i]);
-            }
-            if (a.su) bu += cl * samp * a.su[i];
-            if (two && a.sv) bv += cl * samp * a.sv[i];
-            // shift the history by one level (only the levels the order keeps)
-            if (a.order >= 4) {
-                a.up3[i] = a.up2[i];
-                a.fp3[i] = a.fp2[i];
-            }
-            if (a.order >= 3) {
-                a.up2[i] = a.up[i];
-                a.fp2[i] = a.fp[i];
-            }
-            a.up[i] = ui;
-            a.fp[i] = f;
-            T ru = bu - (c0 * ui - k0 * Lu);
-            V(a, 0, VB)[i] = bu;
-            V(a, 0, VR)[i] = ru;
-            V(a, 0, VRH)[i] = ru;
-            V(a, 0, VP)[i] = T(0);
-            V(a, 0, VQ)[i] = T(0);
-            d[0] += (double)bu * bu;
-            d[1] += (double)ru * ru;
-            if (two) {
-                if (a.order >= 4) {
-                    a.vp3[i] = a.vp2[i];
-                    a.gp3[i] = a.gp2[i];
-                }
-                if (a.order >= 3) {
-                    a.vp2[i] = a.vp[i];
-                    a.gp2[i] = a.gp[i];
-                }
-                a.vp[i] = vi;
-                a.gp[i] = g;
-                T rv = bv - (c0 * vi - k1 * Lv);
-                V(a, 1, VB)[i] = bv;
-                V(a, 1, VR)[i] = rv;
-                V(a, 1, VRH)[i] = rv;
-                V(a, 1, VP)[i] = T(0);
-                V(a, 1, VQ)[i] = T(0);
-                d[3] += (double)bv * bv;
-                d[4] += (double)rv * rv;
-            }
+            rhs_row(a, kc, i, Lu, Lv, d);
         }
         block_partial<6>(d, a.partial, 0);
     }
@@ -580,6 +676,410 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Phase-kernel BiCGSTAB for large operators, replayed from a CUDA graph: the
+// right-hand side (R), then a device-side WHILE loop whose body is one
+// BiCGSTAB iteration as five kernels (A: p; B: q = A p; C: s; D: t = A s;
+// E: x, r), then the report (F).  Kernel boundaries make the vectors
+// coherent, so the SpMV gathers go through L1 (neighbouring rows share most
+// of their stencil nodes) -- inside one cooperative launch they must bypass
+// it -- and no grid barrier is needed.  Reductions: block partials, then the
+// phase's last block (by ticket) sums them in block order (deterministic)
+// and sets the scalars the next phase reads; the last block of E commits
+// the iteration and sets the loop condition.
+// ---------------------------------------------------------------------------
+constexpr int PT = 256;     // threads per block of the SpMV phase kernels (R, B, D)
+constexpr int PT_MINB = 4;  // their resident blocks per SM (<= 64 registers a thread: no spills)
+constexpr int PV = 1024;    // threads per block of the vector phase kernels (A, C, E), one block per SM
+constexpr int VU = 8;       // elements a vector-phase thread loads together (memory-level parallelism)
+constexpr int VUE = 4;      //   in phase E (five vectors: fewer, or registers spill)
+
+// (L x0)_r and (L x1)_r through L1 (x is not written by this kernel); the
+// next chunk's index and weight loads go out before this chunk's gathers,
+// so that a thread has two chunks of the matrix in flight
+template <typename T>
+__device__ __forceinline__ void row_L1(const Args<T>& a, int64_t r, const T* __restrict__ x0,
+                                       const T* __restrict__ x1, bool two, T& y0, T& y1) {
+    const int g = group_of_row(a.gi, r);
+    const int npad = a.gi.npad[g], nch = npad >> 2;
+    const int64_t base = ell_elem(a.gi.ell_off[g], npad, r - a.gi.row_begin[g], 0);
+    T s0 = T(0), s1 = T(0);
+    int4 iv = __ldcs(reinterpret_cast<const int4*>(a.idx + base));
+    T wv[4];
+    load4s(a.w + base, wv);
+    for (int c = 0; c < nch; ++c) {
+        int4 ivn = iv;
+        T wn[4] = {wv[0], wv[1], wv[2], wv[3]};
+        if (c + 1 < nch) {
+            const int64_t en = base + (int64_t)(c + 1) * 128;
+            ivn = __ldcs(reinterpret_cast<const int4*>(a.idx + en));
+            load4s(a.w + en, wn);
+        }
+        const int ii[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            s0 = fma(wv[q], __ldg(x0 + ii[q]), s0);
+            if (two) s1 = fma(wv[q], __ldg(x1 + ii[q]), s1);
+        }
+        iv = ivn;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wv[q] = wn[q];
+    }
+    y0 = s0;
+    y1 = two ? s1 : T(0);
+}
+
+// K sums per block (each thread's accumulators, in float64 from here on)
+// into pp[block][0..K-1]; the last block of the grid sums them in block
+// order into tot[0..K-1] and returns true.  Blocks of NTB <= 1024 threads.
+template <int K, int NTB, typename A>
+__device__ bool phase_reduce(const A (&v)[K], double* pp, double* tot, unsigned int* ticket) {
+    __shared__ double sh[K][NTB / 32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = acc_value(v[k]);
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (int w = 0; w < NTB / 32; ++w) t += sh[threadIdx.x][w];
+        pp[(int64_t)blockIdx.x * 8 + threadIdx.x] = t;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    // fixed order: thread t sums blocks t, t + NTB, ...; then a fixed tree
+    // over the threads' sums
+    __shared__ double acc[K][NTB];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double t = 0.0;
+        for (int64_t b = threadIdx.x; b < gridDim.x; b += NTB) t += __ldcg(pp + b * 8 + k);
+        acc[k][threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int h = NTB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k][threadIdx.x] += acc[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < K) tot[threadIdx.x] = acc[threadIdx.x][0];
+    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ void set_more(PhaseCtl* c, cudaGraphConditionalHandle h, int more) {
+    c->more = more;
+    if (h) cudaGraphSetConditional(h, (unsigned)more);
+}
+
+// beta and the A-decision of the next iteration, from the committed state
+__device__ __forceinline__ void next_iteration(PhaseCtl* c) {
+    for (int k = 0; k < 2; ++k) {
+        c->beta[k] = (c->rho[k] / c->rho_prev[k]) * (c->alpha[k] / c->omega[k]);
+        c->actA[k] = c->active[k] && !(c->rho[k] == 0.0 || !isfinite(c->beta[k]));
+        c->actB[k] = c->early[k] = c->actE[k] = 0;
+    }
+}
+
+// R: right-hand side and r0 (the cooperative kernel's phase R, per row)
+template <typename T>
+__global__ void __launch_bounds__(PT, PT_MINB) phase_R(Args<T> a) {
+    const StepCoef<T> kc = step_coef(a);
+    const bool two = a.ns == 2;
+    typename PhaseAcc<T>::type d[6];
+    for (auto& x : d) acc_zero(x);
+    for (int64_t r = blockIdx.x * (int64_t)PT + threadIdx.x; r < a.N; r += (int64_t)gridDim.x * PT) {
+        const int64_t i = a.row_node[r];
+        T Lu, Lv;
+        row_L1(a, r, a.u, two ? a.v : a.u, two, Lu, Lv);
+        rhs_row(a, kc, i, Lu, Lv, d);
+    }
+    PhaseCtl* c = a.ctl;
+    if (phase_reduce<6, PT>(d, a.pp, c->totR, &c->ticket) && threadIdx.x == 0) {
+        int more = 0;
+        for (int k = 0; k < 2; ++k) {
+            const bool exists = k == 0 || two;
+            const double bn = sqrt(c->totR[3 * k]), rr = c->totR[3 * k + 1];
+            c->bnorm[k] = bn;
+            c->rho[k] = rr;   // (r-hat, r0) = |r0|^2
+            c->rho_prev[k] = c->alpha[k] = c->omega[k] = 1.0;
+            c->relres[k] = bn > 0 ? sqrt(rr) / bn : 0.0;
+            c->conv[k] = !exists || bn == 0.0 || c->relres[k] <= a.tol;
+            c->active[k] = !c->conv[k];
+            c->fail[k] = 0;
+            c->iters[k] = 0;
+            c->zero[k] = exists && bn == 0.0;   // b = 0: x = 0
+            more |= c->active[k];
+        }
+        c->it = 0;
+        next_iteration(c);
+        set_more(c, a.cond, more && a.maxit > 0);
+    }
+}
+
+// The vector phases visit a thread's elements i0, i0 + S, i0 + 2 S, ...
+// (S = the grid's threads) in rounds of VU: a round issues all its loads
+// before any arithmetic, so that a thread has VU loads per vector in flight
+// (the vectors of a large operator are not held in L2 while the SpMV phases
+// stream the matrix through it).  The dot products are summed in the order
+// of the plain grid-stride loop.
+
+// A: p = r + beta (p - omega q)
+template <typename T>
+__global__ void __launch_bounds__(PV) phase_A(Args<T> a) {
+    const PhaseCtl* c = a.ctl;
+    const int64_t S = (int64_t)gridDim.x * PV;
+    for (int k = 0; k < a.ns; ++k) {
+        if (!c->actA[k]) continue;
+        const T beta = (T)c->beta[k], omega = (T)c->omega[k];
+        T* __restrict__ p = V(a, k, VP);
+        const T* __restrict__ r = V(a, k, VR);
+        const T* __restrict__ q = V(a, k, VQ);
+        for (int64_t i0 = blockIdx.x * (int64_t)PV + threadIdx.x; i0 < a.N; i0 += VU * S) {
+            T rv[VU], pv[VU], qv[VU];
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                const int64_t i = i0 + u * S;
+                const bool in = i < a.N;
+                rv[u] = in ? r[i] : T(0);
+                pv[u] = in ? p[i] : T(0);
+                qv[u] = in ? q[i] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                const int64_t i = i0 + u * S;
+                if (i < a.N) p[i] = rv[u] + beta * (pv[u] - omega * qv[u]);
+            }
+        }
+    }
+}
+
+// B: q = A p ; (r-hat, q)
+template <typename T>
+__global__ void __launch_bounds__(PT, PT_MINB) phase_B(Args<T> a) {
+    PhaseCtl* c = a.ctl;
+    const bool a0 = c->actA[0], a1 = a.ns == 2 && c->actA[1];
+    const StepCoef<T> kc = step_coef(a);
+    typename PhaseAcc<T>::type d[2];
+    for (auto& x : d) acc_zero(x);
+    for (int64_t r = blockIdx.x * (int64_t)PT + threadIdx.x; (a0 || a1) && r < a.N; r += (int64_t)gridDim.x * PT) {
+        const int64_t i = a.row_node[r];
+        T L0, L1;
+        row_L1(a, r, V(a, 0, VP), a.ns == 2 ? V(a, 1, VP) : V(a, 0, VP), a1, L0, L1);
+        if (a0) {
+            const T q = kc.c0 * V(a, 0, VP)[i] - kc.k0 * L0;
+            V(a, 0, VQ)[i] = q;
+            acc_add(d[0], V(a, 0, VRH)[i], q);
+        }
+        if (a1) {
+            const T q = kc.c0 * V(a, 1, VP)[i] - kc.k1 * L1;
+            V(a, 1, VQ)[i] = q;
+            acc_add(d[1], V(a, 1, VRH)[i], q);
+        }
+    }
+    if (phase_reduce<2, PT>(d, a.pp, c->totB, &c->ticket) && threadIdx.x == 0)
+        for (int k = 0; k < 2; ++k) {
+            c->alpha_n[k] = c->actA[k] ? c->rho[k] / c->totB[k] : 0.0;
+            c->actB[k] = c->actA[k] && !(c->totB[k] == 0.0 || !isfinite(c->alpha_n[k]));
+        }
+}
+
+// C: s = r - alpha q ; |s|^2
+template <typename T>
+__global__ void __launch_bounds__(PV) phase_C(Args<T> a) {
+    PhaseCtl* c = a.ctl;
+    typename PhaseAcc<T>::type d[2];
+    for (auto& x : d) acc_zero(x);
+    const int64_t S = (int64_t)gridDim.x * PV;
+    for (int k = 0; k < a.ns; ++k) {
+        if (!c->actB[k]) continue;
+        const T alpha = (T)c->alpha_n[k];
+        const T* __restrict__ r = V(a, k, VR);
+        const T* __restrict__ q = V(a, k, VQ);
+        T* __restrict__ sv = V(a, k, VS);
+        for (int64_t i0 = blockIdx.x * (int64_t)PV + threadIdx.x; i0 < a.N; i0 += VU * S) {
+            T rv[VU], qv[VU];
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                const int64_t i = i0 + u * S;
+                const bool in = i < a.N;
+                rv[u] = in ? r[i] : T(0);
+                qv[u] = in ? q[i] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                const int64_t i = i0 + u * S;
+                if (i < a.N) {
+                    const T x = rv[u] - alpha * qv[u];
+                    sv[i] = x;
+                    acc_add(d[k], x, x);
+                }
+            }
+        }
+    }
+    if (phase_reduce<2, PV>(d, a.pp, c->totC, &c->ticket) && threadIdx.x == 0)
+        for (int k = 0; k < 2; ++k) c->early[k] = c->actB[k] && sqrt(c->totC[k]) / c->bnorm[k] <= a.tol;
+}
+
+// D: t = A s ; (t, s), (t, t)   (x += alpha p where s already converged)
+template <typename T>
+__global__ void __launch_bounds__(PT, PT_MINB) phase_D(Args<T> a) {
+    PhaseCtl* c = a.ctl;
+    const StepCoef<T> kc = step_coef(a);
+    const bool two = a.ns == 2;
+    const bool e0 = c->early[0], e1 = two && c->early[1];
+    const bool b0 = c->actB[0], b1 = two && c->actB[1];
+    const bool need0 = b0 && !e0, need1 = b1 && !e1;
+    typename PhaseAcc<T>::type d[4];
+    for (auto& x : d) acc_zero(x);
+    for (int64_t r = blockIdx.x * (int64_t)PT + threadIdx.x; (b0 || b1) && r < a.N; r += (int64_t)gridDim.x * PT) {
+        const int64_t i = a.row_node[r];
+        T L0 = T(0), L1 = T(0);
+        if (need0 || need1) row_L1(a, r, V(a, 0, VS), two ? V(a, 1, VS) : V(a, 0, VS), need1, L0, L1);
+        for (int k = 0; k < a.ns; ++k) {
+            T* x = k == 0 ? a.u : a.v;
+            if (k == 0 ? e0 : e1) {
+                x[i] += (T)c->alpha_n[k] * V(a, k, VP)[i];
+            } else if (k == 0 ? b0 : b1) {
+                const T sv = V(a, k, VS)[i];
+                const T t = kc.c0 * sv - (k == 0 ? kc.k0 * L0 : kc.k1 * L1);
+                V(a, k, VT)[i] = t;
+                acc_add(d[2 * k], t, sv);
+                acc_add(d[2 * k + 1], t, t);
+            }
+        }
+    }
+    if (phase_reduce<4, PT>(d, a.pp, c->totD, &c->ticket) && threadIdx.x == 0)
+        for (int k = 0; k < 2; ++k) {
+            c->omega_n[k] = c->totD[2 * k] / c->totD[2 * k + 1];
+            c->actE[k] = c->actB[k] && !c->early[k] && !(c->totD[2 * k + 1] == 0.0 || !isfinite(c->omega_n[k]));
+        }
+}
+
+// E: x += alpha p + omega s ; r = s - omega t ; (r-hat, r), |r|^2; the last
+// block commits the iteration and decides whether the loop continues
+template <typename T>
+__global__ void __launch_bounds__(PV) phase_E(Args<T> a) {
+    PhaseCtl* c = a.ctl;
+    typename PhaseAcc<T>::type d[4];
+    for (auto& x : d) acc_zero(x);
+    const int64_t S = (int64_t)gridDim.x * PV;
+    for (int k = 0; k < a.ns; ++k) {
+        if (!c->actE[k]) continue;
+        const T alpha = (T)c->alpha_n[k], omega = (T)c->omega_n[k];
+        T* __restrict__ x = k == 0 ? a.u : a.v;
+        const T* __restrict__ p = V(a, k, VP);
+        const T* __restrict__ sv = V(a, k, VS);
+        const T* __restrict__ t = V(a, k, VT);
+        const T* __restrict__ rh = V(a, k, VRH);
+        T* __restrict__ r = V(a, k, VR);
+        for (int64_t i0 = blockIdx.x * (int64_t)PV + threadIdx.x; i0 < a.N; i0 += VUE * S) {
+            T xv[VUE], pv[VUE], s_[VUE], tv[VUE], hv[VUE];
+#pragma unroll
+            for (int u = 0; u < VUE; ++u) {
+                const int64_t i = i0 + u * S;
+                const bool in = i < a.N;
+                xv[u] = in ? x[i] : T(0);
+                pv[u] = in ? p[i] : T(0);
+                s_[u] = in ? sv[i] : T(0);
+                tv[u] = in ? t[i] : T(0);
+                hv[u] = in ? rh[i] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < VUE; ++u) {
+                const int64_t i = i0 + u * S;
+                if (i < a.N) {
+                    x[i] = xv[u] + (alpha * pv[u] + omega * s_[u]);
+                    const T rn = s_[u] - omega * tv[u];
+                    r[i] = rn;
+                    acc_add(d[2 * k], hv[u], rn);
+                    acc_add(d[2 * k + 1], rn, rn);
+                }
+            }
+        }
+    }
+    if (phase_reduce<4, PV>(d, a.pp, c->totE, &c->ticket) && threadIdx.x == 0) {
+        const int it = c->it + 1;
+        int more = 0;
+        for (int k = 0; k < 2; ++k) {
+            if (!c->active[k]) continue;
+            if (!c->actA[k] || !c->actB[k]) {
+                c->fail[k] = 1;
+                c->active[k] = 0;
+            } else if (c->early[k]) {
+                c->relres[k] = sqrt(c->totC[k]) / c->bnorm[k];
+                c->conv[k] = 1;
+                c->active[k] = 0;
+                c->iters[k] = it;
+            } else if (!c->actE[k]) {
+                c->fail[k] = 1;
+                c->active[k] = 0;
+            } else {
+                c->rho_prev[k] = c->rho[k];
+                c->rho[k] = c->totE[2 * k];
+                c->alpha[k] = c->alpha_n[k];
+                c->omega[k] = c->omega_n[k];
+                c->relres[k] = sqrt(c->totE[2 * k + 1]) / c->bnorm[k];
+                if (c->relres[k] <= a.tol) {
+                    c->conv[k] = 1;
+                    c->active[k] = 0;
+                    c->iters[k] = it;
+                } else if (c->omega_n[k] == 0.0) {
+                    c->fail[k] = 1;
+                    c->active[k] = 0;
+                }
+            }
+            more |= c->active[k];
+        }
+        c->it = it;
+        next_iteration(c);
+        set_more(c, a.cond, more && it < a.maxit);
+    }
+}
+
+// F: report of the step, history flags, x = 0 where b = 0
+template <typename T>
+__global__ void __launch_bounds__(PT) phase_F(Args<T> a) {
+    const PhaseCtl* c = a.ctl;
+    for (int k = 0; k < a.ns; ++k) {
+        if (!c->zero[k]) continue;
+        T* x = k == 0 ? a.u : a.v;
+        for (int64_t i = blockIdx.x * (int64_t)PT + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * PT) x[i] = T(0);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const StepCoef<T> kc = step_coef(a);
+        int iters[2] = {c->iters[0], c->iters[1]};
+        bool bad = false;
+        for (int k = 0; k < 2; ++k) {
+            if (c->active[k]) {   // hit maxit
+                iters[k] = c->it;
+                bad = true;
+            }
+            if (c->fail[k]) bad = true;
+        }
+        int* rp = a.rep + (int64_t)kc.slot * 3;
+        rp[0] = iters[0];
+        rp[1] = iters[1];
+        rp[2] = bad ? 1 : 0;
+        a.rep_res[(int64_t)kc.slot * 2] = c->relres[0];
+        a.rep_res[(int64_t)kc.slot * 2 + 1] = c->relres[1];
+        if (bad) atomicExch(a.flags + 1, 1);
+        a.flags[2] = min(kc.nhist + 1, max(a.order - 1, 1));
+        a.flags[3] = kc.slot + 1;
+        a.flags[4] = kc.ord;
+    }
+}
+
 __global__ void lonely_barrier(unsigned long long* bar, int* err) {
     // a second arrival never comes: the bounded wait must give up
     grid_sync(bar, 2ull * gridDim.x, err);
@@ -626,6 +1126,9 @@ void fill_args(Args<T>& a, rbffd_op* op, rbffd_state* s, const rbffd_step_params
     a.rep = ws->rep;
     a.rep_res = ws->rep_res;
     a.rhs_only = p->solver == RBFFD_SOLVER_BANDED_LU ? 1 : 0;
+    a.ctl = ws->ctl;
+    a.pp = ws->pp;
+    a.cond = 0;
 }
 
 template <typename T>
@@ -648,10 +1151,130 @@ rbffd_status launch_step(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
     return RBFFD_OK;
 }
 
+// resident-sized grids, grid-stride loops: the SpMV phases PT_MINB blocks
+// of PT threads per SM (their register bound makes exactly that many fit:
+// one wave, no partial second one), the vector phases one block of PV
+// threads per SM.  (A grid of one thread per row or element ran slower:
+// the per-block reduction and ticket then cost more than a block's work.)
+// The per-block partials (pp) hold ceil(N / PT) blocks, more than either grid.
+template <typename T>
+void phase_grids(const Args<T>& a, unsigned* g_rows, unsigned* g_vec) {
+    *g_rows = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.N + PT - 1) / PT, (int64_t)sm_count() * PT_MINB));
+    *g_vec = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.N + PV - 1) / PV, (int64_t)sm_count()));
+}
+
+// One step of the phase-kernel path from the host (no graph): R, then the
+// iterations while the loop state says so (the condition is read back after
+// each iteration), then F -- the same kernels and arithmetic as the graph.
+template <typename T>
+rbffd_status phased_step_host(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
+    unsigned gr, gv;
+    phase_grids(a, &gr, &gv);
+    a.cond = 0;
+    phase_R<T><<<gr, PT, 0, st>>>(a);
+    note_launch();
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    for (;;) {
+        int more = 0;
+        RBFFD_CUDA_TRY(cudaMemcpyAsync(&more, &ws->ctl->more, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RBFFD_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!more) break;
+        phase_A<T><<<gv, PV, 0, st>>>(a);
+        phase_B<T><<<gr, PT, 0, st>>>(a);
+        phase_C<T><<<gv, PV, 0, st>>>(a);
+        phase_D<T><<<gr, PT, 0, st>>>(a);
+        phase_E<T><<<gv, PV, 0, st>>>(a);
+        note_launch(5);
+        RBFFD_CUDA_TRY(cudaGetLastError());
+    }
+    phase_F<T><<<gr, PT, 0, st>>>(a);
+    note_launch();
+    RBFFD_CUDA_TRY(cudaGetLastError());
+    return RBFFD_OK;
+}
+
+// The step as a graph: R -> WHILE (condition set on the device) { A B C D E } -> F
+template <typename T>
+rbffd_status build_phase_graph(Args<T> a, cudaGraphExec_t* out) {
+    unsigned gr, gv;
+    phase_grids(a, &gr, &gv);
+    cudaGraph_t g = nullptr;
+    RBFFD_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        RBFFD_CUDA_TRY(e);
+    }
+    a.cond = h;
+    void* args[] = {&a};
+    auto kernel = [&](cudaGraph_t graph, const void* fn, bool vec, cudaGraphNode_t* dep, cudaGraphNode_t* node) {
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = const_cast<void*>(fn);
+        kp.gridDim = dim3(vec ? gv : gr);
+        kp.blockDim = dim3(vec ? PV : PT);
+        kp.kernelParams = args;
+        return cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &kp);
+    };
+    cudaGraphNode_t nR, nW, nF;
+    e = kernel(g, (const void*)phase_R<T>, false, nullptr, &nR);
+    // (the parameter union has no default constructor: zeroed raw storage)
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&nW, g, &nR, nullptr, 1, &cp);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t n1, n2, n3, n4, n5;
+        e = kernel(body, (const void*)phase_A<T>, true, nullptr, &n1);
+        if (e == cudaSuccess) e = kernel(body, (const void*)phase_B<T>, false, &n1, &n2);
+        if (e == cudaSuccess) e = kernel(body, (const void*)phase_C<T>, true, &n2, &n3);
+        if (e == cudaSuccess) e = kernel(body, (const void*)phase_D<T>, false, &n3, &n4);
+        if (e == cudaSuccess) e = kernel(body, (const void*)phase_E<T>, true, &n4, &n5);
+    }
+    if (e == cudaSuccess) e = kernel(g, (const void*)phase_F<T>, false, &nW, &nF);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    RBFFD_CUDA_TRY(e);
+    return RBFFD_OK;
+}
+
 // nsteps launches, directly or by replaying one captured graph of a step
 template <typename T>
 rbffd_status run_steps(Args<T>& a, rbffd_step_ws* ws, int64_t nsteps, bool use_graph, cudaStream_t st) {
     static_assert(sizeof(Args<T>) <= sizeof(ws->graph_args), "graph key too small");
+    if (ws->phased && !a.rhs_only) {
+        if (!use_graph) {
+            for (int64_t k = 0; k < nsteps; ++k) {
+                rbffd_status r = phased_step_host(a, ws, st);
+                if (r != RBFFD_OK) return r;
+            }
+            return RBFFD_OK;
+        }
+        a.cond = 0;   // the graph key holds the arguments without the handle
+        if (!ws->graph || ws->graph_args_size != sizeof(a) || memcmp(ws->graph_args, &a, sizeof(a)) != 0 ||
+            ws->solver != 2) {
+            if (ws->graph) {
+                cudaGraphExecDestroy(ws->graph);
+                ws->graph = nullptr;
+            }
+            rbffd_status r = build_phase_graph(a, &ws->graph);
+            if (r != RBFFD_OK) return r;
+            memcpy(ws->graph_args, &a, sizeof(a));
+            ws->graph_args_size = sizeof(a);
+            ws->solver = 2;
+        }
+        for (int64_t k = 0; k < nsteps; ++k) {
+            RBFFD_CUDA_TRY(cudaGraphLaunch(ws->graph, st));
+            note_launch(2);   // R and F; the loop body's five per iteration are counted from the report
+        }
+        return RBFFD_OK;
+    }
     if (!use_graph) {
         for (int64_t k = 0; k < nsteps; ++k) {
             rbffd_status r = launch_step(a, ws, st);
@@ -662,7 +1285,7 @@ rbffd_status run_steps(Args<T>& a, rbffd_step_ws* ws, int64_t nsteps, bool use_g
     // the graph holds the kernels' arguments, the LU solve's factor pointers
     // included: any change recaptures it
     if (!ws->graph || ws->graph_args_size != sizeof(a) || memcmp(ws->graph_args, &a, sizeof(a)) != 0 ||
-        ws->solver != a.rhs_only || memcmp(ws->graph_lu, ws->lu, sizeof(ws->lu)) != 0) {
+        ws->solver != a.rhs_only || memcmp(ws->graph_lu, ws->lu, sizeof(ws->lu)) != 0 || ws->solver == 2) {
         if (ws->graph) {
             cudaGraphExecDestroy(ws->graph);
             ws->graph = nullptr;
@@ -753,6 +1376,14 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         RBFFD_CUDA_TRY(cudaMalloc(&ws->bar, sizeof(unsigned long long)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->flags, 5 * sizeof(int)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->tstart, sizeof(double)));
+        // large operators: BiCGSTAB as phase kernels under a device-side
+        // loop (SpMV gathers through L1, full occupancy); small ones: the
+        // cooperative kernel (a few blocks, latency-bound, where one launch
+        // per step wins)
+        ws->phased = ws->threads == 1024 ? 1 : 0;
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->ctl, sizeof(PhaseCtl)));
+        RBFFD_CUDA_TRY(cudaMemset(ws->ctl, 0, sizeof(PhaseCtl)));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->pp, (size_t)std::max<int64_t>(1, (op->N + PT - 1) / PT) * 8 * sizeof(double)));
         ws->rep_cap = 0;
     }
     if (ws->rep_cap < std::max<int64_t>(nsteps, 1)) {
@@ -833,6 +1464,8 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         r.last_relres_u = res[2 * k];
         r.last_relres_v = res[2 * k + 1];
     }
+    if (ws->phased && p->use_graph && p->solver == RBFFD_SOLVER_BICGSTAB)
+        for (int64_t k = 0; k < nsteps; ++k) note_launch(5 * std::max(rep[3 * k], rep[3 * k + 1]));
     r.steps_done = nsteps;
     s->has_history = (int)std::min<int64_t>((int64_t)std::min(s->has_history, kept) + nsteps, kept);
     s->step += nsteps;

@@ -1,6 +1,7 @@
 """GPU parity of the IMEX stepper (reaction + SBDF2 right-hand side +
-BiCGSTAB, one cooperative launch per step) against the oracle's stepper on
-the same operator.
+BiCGSTAB: one cooperative launch per step for small operators, phase kernels
+under a device-side loop for large ones) against the oracle's stepper on the
+same operator.
 
 Tolerances: float64 stepping at BiCGSTAB tolerance 1e-12 matches the oracle
 to 1e-9 relative (both solve the same systems to 1e-12; the difference is
@@ -313,3 +314,64 @@ def test_invalid_step_parameters_are_rejected(R):
         assert e.value.status == 1, kw
     with pytest.raises(R.RbffdError):     # two species without the v state
         R.step_imex(op, st, R.StepParams(model="none", nspecies=2, dtype=torch.float64, dt=1e-3), 1)
+
+
+def _csr_rows(R, op, N):
+    import scipy.sparse as sps
+    idx, w = (t.cpu().numpy() for t in R.get_rows(op))
+    n = idx.shape[1]
+    return sps.csr_matrix((w.ravel(), (np.repeat(np.arange(N), n), idx.ravel())), shape=(N, N))
+
+
+@pytest.fixture(scope="module")
+def sphere200k(R):
+    """200k-node Fibonacci sphere, n = 31, IMQ at a fixed eps: above the
+    size (1024 rows per SM) where the stepper switches to the phase-kernel
+    path.  The oracle steps with the same operator (its rows as a sparse
+    matrix): the parity checked is the stepper's."""
+    ns = W.fibonacci_sphere(200_000)
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="imq",
+                          eps_override=T(np.full(ns.N, 2.5 * math.sqrt(ns.N / 2562.0))))
+    return ns, op, _csr_rows(R, op, ns.N)
+
+
+@pytest.mark.parametrize("dtype,tol,bound", [(torch.float64, 1e-12, 1e-9), (torch.float32, 1e-8, 1e-5)])
+def test_phase_kernel_path_large_operator(R, sphere200k, dtype, tol, bound):
+    """Schnakenberg, 20 SBDF2 steps on the phase-kernel path: against the
+    oracle's BiCGSTAB steps on the same operator (float64 1e-9, float32
+    1e-5: the bars of the cooperative path); the WHILE-graph replay and the
+    host-driven loop of the same kernels give the same bits; the loop
+    launches five kernels per iteration (the launch counter)."""
+    ns, op, L = sphere200k
+    s = W.SCHNAKENBERG
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=4)
+    name, coef = R.model_coefs(s)
+    out = []
+    for graph in (True, False):
+        p = R.StepParams(model=name, nspecies=2, dtype=dtype, dt=s["dt"], delta_u=s["delta_u"],
+                         delta_v=s["delta_v"], coef=coef, tol=tol, use_graph=graph)
+        st = R.StepState.create(T(u0, dtype), T(v0, dtype))
+        n0 = R.launch_count()
+        rep = R.step_imex(op, st, p, 20)
+        launches = R.launch_count() - n0
+        assert rep["status"] == 0
+        assert rep["max_iters_u"] >= 1 and launches >= 20 * (2 + 5)
+        out.append((st.u.clone(), st.v.clone()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    o = ostp.imex_run(lambda x: L @ x, u0, v0, s, 20)
+    assert rel_inf(out[0][0].cpu().numpy().astype(np.float64), o["u"]) <= bound
+    assert rel_inf(out[0][1].cpu().numpy().astype(np.float64), o["v"]) <= bound
+
+
+def test_phase_kernel_path_one_species_heat(R, sphere200k):
+    """One species (the second species' branches off): float64 heat
+    equation, 30 SBDF2 steps of Y_3^2 on the phase-kernel path against the
+    oracle's steps on the same operator, 1e-9."""
+    ns, op, L = sphere200k
+    u0 = W.sph_harm_y32(ns.X)
+    p = R.StepParams(model="none", nspecies=1, dtype=torch.float64, dt=1e-4, delta_u=1.0, tol=1e-12)
+    st = R.StepState.create(T(u0))
+    rep = R.step_imex(op, st, p, 30)
+    assert rep["status"] == 0 and rep["max_iters_v"] == 0
+    o = ostp.imex_run(lambda x: L @ x, u0, None, dict(model="none", dt=1e-4, delta_u=1.0), 30)
+    assert rel_inf(st.u.cpu().numpy(), o["u"]) <= 1e-9
