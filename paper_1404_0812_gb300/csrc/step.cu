@@ -54,7 +54,7 @@ struct rbffd_step_ws {
     int dtype;
     int64_t N;
     size_t elem;
-    void* vec;                     // 2 species x 7 vectors (b, r, rh, p, q, s, t)
+    void* vec;                     // 2 species x 7 vectors (b, r, rh, p, q, s, t), each padded to a multiple of 4
     double* partial;               // phases x blocks x 8
     unsigned long long* bar;       // barrier counter
     int* flags;                    // [0] error (timeout), [1] not converged, [2] has_history,
@@ -117,7 +117,9 @@ struct Args {
     const T *su, *sv;  // source profiles h_u, h_v (or NULL): s(t) = exp(rate t) h
     double src_rate;
     const double* tstart;   // time of u when the call began
-    T* vec;            // 2 x 7 x N
+    T* vec;            // 2 x 7 vectors of ldv elements
+    int64_t ldv;       // their stride: N rounded up to a multiple of 4 (16-byte aligned vectors)
+    int vec4;          // the state u (and v) 16-byte aligned: the vector phases move 4 elements at a time
     int ns;
     int model;
     T c[8];
@@ -140,7 +142,7 @@ enum { VB = 0, VR = 1, VRH = 2, VP = 3, VQ = 4, VS = 5, VT = 6 };
 
 template <typename T>
 __host__ __device__ __forceinline__ T* V(const Args<T>& a, int sp, int k) {
-    return a.vec + ((int64_t)sp * 7 + k) * a.N;
+    return a.vec + ((int64_t)sp * 7 + k) * a.ldv;
 }
 
 template <typename T>
@@ -690,24 +692,45 @@ __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
 // ---------------------------------------------------------------------------
 constexpr int PT = 256;     // threads per block of the SpMV phase kernels (R, B, D)
 constexpr int PT_MINB = 4;  // their resident blocks per SM (<= 64 registers a thread: no spills)
-constexpr int PV = 1024;    // threads per block of the vector phase kernels (A, C, E), one block per SM
-constexpr int VU = 8;       // elements a vector-phase thread loads together (memory-level parallelism)
-constexpr int VUE = 4;      //   in phase E (five vectors: fewer, or registers spill)
+constexpr int PV = 256;    // threads per block of the vector phase kernels (A, C, E)
+constexpr int PV_BPS = 4;   //   and their blocks per SM
+constexpr int VG = 2;       // four-element groups a thread of phases A and C loads together
 
 // (L x0)_r and (L x1)_r through L1 (x is not written by this kernel); the
 // next chunk's index and weight loads go out before this chunk's gathers,
-// so that a thread has two chunks of the matrix in flight
+// so that a thread has two chunks of the matrix in flight, and with
+// ROW_PF > 0 an L2 prefetch ROW_PF chunks ahead runs on into the thread's
+// next row (rnext)
+constexpr int ROW_PF = 2;
+
 template <typename T>
-__device__ __forceinline__ void row_L1(const Args<T>& a, int64_t r, const T* __restrict__ x0,
+__device__ __forceinline__ void row_L1(const Args<T>& a, int64_t r, int64_t rnext, const T* __restrict__ x0,
                                        const T* __restrict__ x1, bool two, T& y0, T& y1) {
     const int g = group_of_row(a.gi, r);
     const int npad = a.gi.npad[g], nch = npad >> 2;
     const int64_t base = ell_elem(a.gi.ell_off[g], npad, r - a.gi.row_begin[g], 0);
+    int64_t nbase = -1;
+    int nnch = 0;
+    if (ROW_PF > 0 && rnext < a.N) {
+        const int gn = group_of_row(a.gi, rnext);
+        nnch = a.gi.npad[gn] >> 2;
+        nbase = ell_elem(a.gi.ell_off[gn], a.gi.npad[gn], rnext - a.gi.row_begin[gn], 0);
+    }
     T s0 = T(0), s1 = T(0);
     int4 iv = __ldcs(reinterpret_cast<const int4*>(a.idx + base));
     T wv[4];
     load4s(a.w + base, wv);
     for (int c = 0; c < nch; ++c) {
+        if (ROW_PF > 0) {
+            const int k = c + ROW_PF;
+            int64_t e = -1;
+            if (k < nch) e = base + (int64_t)k * 128;
+            else if (k - nch < nnch && nbase >= 0) e = nbase + (int64_t)(k - nch) * 128;
+            if (e >= 0) {
+                prefetch_l2(a.idx + e);
+                prefetch_l2(a.w + e);
+            }
+        }
         int4 ivn = iv;
         T wn[4] = {wv[0], wv[1], wv[2], wv[3]};
         if (c + 1 < nch) {
@@ -801,7 +824,7 @@ __global__ void __launch_bounds__(PT, PT_MINB) phase_R(Args<T> a) {
     for (int64_t r = blockIdx.x * (int64_t)PT + threadIdx.x; r < a.N; r += (int64_t)gridDim.x * PT) {
         const int64_t i = a.row_node[r];
         T Lu, Lv;
-        row_L1(a, r, a.u, two ? a.v : a.u, two, Lu, Lv);
+        row_L1(a, r, r + (int64_t)gridDim.x * PT, a.u, two ? a.v : a.u, two, Lu, Lv);
         rhs_row(a, kc, i, Lu, Lv, d);
     }
     PhaseCtl* c = a.ctl;
@@ -827,44 +850,78 @@ __global__ void __launch_bounds__(PT, PT_MINB) phase_R(Args<T> a) {
     }
 }
 
-// The vector phases visit a thread's elements i0, i0 + S, i0 + 2 S, ...
-// (S = the grid's threads) in rounds of VU: a round issues all its loads
-// before any arithmetic, so that a thread has VU loads per vector in flight
-// (the vectors of a large operator are not held in L2 while the SpMV phases
-// stream the matrix through it).  The dot products are summed in the order
-// of the plain grid-stride loop.
+// The vector phases move groups of four consecutive elements with 16-byte
+// loads and stores (every internal vector starts on a 16-byte boundary; the
+// state u, v when the caller's are aligned, else a plain element loop): a
+// quarter of the memory instructions and of the index arithmetic of an
+// element loop, whose instruction count bounded them.  A thread visits
+// groups g0, g0 + S, ... (S = the grid's threads), VG at a time with all
+// their loads issued first; the last N mod 4 elements go element by
+// element.  The dot products are summed per thread in that order.
+
+__device__ __forceinline__ void ld4v(const float* p, float (&w)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+__device__ __forceinline__ void ld4v(const double* p, double (&w)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+__device__ __forceinline__ void st4v(float* p, const float (&w)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ void st4v(double* p, const double (&w)[4]) {
+    *reinterpret_cast<double2*>(p) = make_double2(w[0], w[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(w[2], w[3]);
+}
 
 // A: p = r + beta (p - omega q)
 template <typename T>
-__global__ void __launch_bounds__(PV) phase_A(Args<T> a) {
+__global__ void __launch_bounds__(PV, PV_BPS) phase_A(Args<T> a) {
     const PhaseCtl* c = a.ctl;
-    const int64_t S = (int64_t)gridDim.x * PV;
+    const int64_t S = (int64_t)gridDim.x * PV, t0 = blockIdx.x * (int64_t)PV + threadIdx.x;
     for (int k = 0; k < a.ns; ++k) {
         if (!c->actA[k]) continue;
         const T beta = (T)c->beta[k], omega = (T)c->omega[k];
         T* __restrict__ p = V(a, k, VP);
         const T* __restrict__ r = V(a, k, VR);
         const T* __restrict__ q = V(a, k, VQ);
-        for (int64_t i0 = blockIdx.x * (int64_t)PV + threadIdx.x; i0 < a.N; i0 += VU * S) {
-            T rv[VU], pv[VU], qv[VU];
+        int64_t i = t0;
+        if (a.vec4) {
+            const int64_t G = a.N >> 2;
+            for (int64_t g0 = t0; g0 < G; g0 += VG * S) {
+                T rv[VG][4], pv[VG][4], qv[VG][4];
 #pragma unroll
-            for (int u = 0; u < VU; ++u) {
-                const int64_t i = i0 + u * S;
-                const bool in = i < a.N;
-                rv[u] = in ? r[i] : T(0);
-                pv[u] = in ? p[i] : T(0);
-                qv[u] = in ? q[i] : T(0);
-            }
+                for (int u = 0; u < VG; ++u)
+                    if (g0 + u * S < G) {
+                        const int64_t e = 4 * (g0 + u * S);
+                        ld4v(r + e, rv[u]);
+                        ld4v(p + e, pv[u]);
+                        ld4v(q + e, qv[u]);
+                    }
 #pragma unroll
-            for (int u = 0; u < VU; ++u) {
-                const int64_t i = i0 + u * S;
-                if (i < a.N) p[i] = rv[u] + beta * (pv[u] - omega * qv[u]);
+                for (int u = 0; u < VG; ++u)
+                    if (g0 + u * S < G) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) pv[u][j] = rv[u][j] + beta * (pv[u][j] - omega * qv[u][j]);
+                        st4v(p + 4 * (g0 + u * S), pv[u]);
+                    }
             }
+            i = 4 * G + t0;
         }
+        for (; i < a.N; i += S) p[i] = r[i] + beta * (p[i] - omega * q[i]);
     }
 }
 
-// B: q = A p ; (r-hat, q)
+// B: q = A p ; (r-hat, q).  With B_BACK it visits the rows from the last
+// 32-row slice to the first (lanes keep their order within a slice): R and D
+// run forward, so every pass over the matrix starts on the rows the pass
+// before it ended on, which are still in L2.
+constexpr bool B_BACK = true;
+
+__device__ __forceinline__ int64_t back_row(int64_t k, int64_t Np) { return Np - 32 - (k & ~(int64_t)31) + (k & 31); }
+
 template <typename T>
 __global__ void __launch_bounds__(PT, PT_MINB) phase_B(Args<T> a) {
     PhaseCtl* c = a.ctl;
@@ -872,10 +929,14 @@ __global__ void __launch_bounds__(PT, PT_MINB) phase_B(Args<T> a) {
     const StepCoef<T> kc = step_coef(a);
     typename PhaseAcc<T>::type d[2];
     for (auto& x : d) acc_zero(x);
-    for (int64_t r = blockIdx.x * (int64_t)PT + threadIdx.x; (a0 || a1) && r < a.N; r += (int64_t)gridDim.x * PT) {
+    const int64_t S = (int64_t)gridDim.x * PT, Np = (a.N + 31) & ~(int64_t)31;
+    for (int64_t k = blockIdx.x * (int64_t)PT + threadIdx.x; (a0 || a1) && k < Np; k += S) {
+        const int64_t r = B_BACK ? back_row(k, Np) : k;
+        if (r >= a.N) continue;
+        const int64_t rn = k + S >= Np ? a.N : (B_BACK ? back_row(k + S, Np) : k + S);
         const int64_t i = a.row_node[r];
         T L0, L1;
-        row_L1(a, r, V(a, 0, VP), a.ns == 2 ? V(a, 1, VP) : V(a, 0, VP), a1, L0, L1);
+        row_L1(a, r, rn, V(a, 0, VP), a.ns == 2 ? V(a, 1, VP) : V(a, 0, VP), a1, L0, L1);
         if (a0) {
             const T q = kc.c0 * V(a, 0, VP)[i] - kc.k0 * L0;
             V(a, 0, VQ)[i] = q;
@@ -896,35 +957,46 @@ __global__ void __launch_bounds__(PT, PT_MINB) phase_B(Args<T> a) {
 
 // C: s = r - alpha q ; |s|^2
 template <typename T>
-__global__ void __launch_bounds__(PV) phase_C(Args<T> a) {
+__global__ void __launch_bounds__(PV, PV_BPS) phase_C(Args<T> a) {
     PhaseCtl* c = a.ctl;
     typename PhaseAcc<T>::type d[2];
     for (auto& x : d) acc_zero(x);
-    const int64_t S = (int64_t)gridDim.x * PV;
+    const int64_t S = (int64_t)gridDim.x * PV, t0 = blockIdx.x * (int64_t)PV + threadIdx.x;
     for (int k = 0; k < a.ns; ++k) {
         if (!c->actB[k]) continue;
         const T alpha = (T)c->alpha_n[k];
         const T* __restrict__ r = V(a, k, VR);
         const T* __restrict__ q = V(a, k, VQ);
         T* __restrict__ sv = V(a, k, VS);
-        for (int64_t i0 = blockIdx.x * (int64_t)PV + threadIdx.x; i0 < a.N; i0 += VU * S) {
-            T rv[VU], qv[VU];
+        int64_t i = t0;
+        if (a.vec4) {
+            const int64_t G = a.N >> 2;
+            for (int64_t g0 = t0; g0 < G; g0 += VG * S) {
+                T rv[VG][4], qv[VG][4];
 #pragma unroll
-            for (int u = 0; u < VU; ++u) {
-                const int64_t i = i0 + u * S;
-                const bool in = i < a.N;
-                rv[u] = in ? r[i] : T(0);
-                qv[u] = in ? q[i] : T(0);
-            }
+                for (int u = 0; u < VG; ++u)
+                    if (g0 + u * S < G) {
+                        const int64_t e = 4 * (g0 + u * S);
+                        ld4v(r + e, rv[u]);
+                        ld4v(q + e, qv[u]);
+                    }
 #pragma unroll
-            for (int u = 0; u < VU; ++u) {
-                const int64_t i = i0 + u * S;
-                if (i < a.N) {
-                    const T x = rv[u] - alpha * qv[u];
-                    sv[i] = x;
-                    acc_add(d[k], x, x);
-                }
+                for (int u = 0; u < VG; ++u)
+                    if (g0 + u * S < G) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            rv[u][j] = rv[u][j] - alpha * qv[u][j];
+                            acc_add(d[k], rv[u][j], rv[u][j]);
+                        }
+                        st4v(sv + 4 * (g0 + u * S), rv[u]);
+                    }
             }
+            i = 4 * G + t0;
+        }
+        for (; i < a.N; i += S) {
+            const T x = r[i] - alpha * q[i];
+            sv[i] = x;
+            acc_add(d[k], x, x);
         }
     }
     if (phase_reduce<2, PV>(d, a.pp, c->totC, &c->ticket) && threadIdx.x == 0)
@@ -945,7 +1017,7 @@ __global__ void __launch_bounds__(PT, PT_MINB) phase_D(Args<T> a) {
     for (int64_t r = blockIdx.x * (int64_t)PT + threadIdx.x; (b0 || b1) && r < a.N; r += (int64_t)gridDim.x * PT) {
         const int64_t i = a.row_node[r];
         T L0 = T(0), L1 = T(0);
-        if (need0 || need1) row_L1(a, r, V(a, 0, VS), two ? V(a, 1, VS) : V(a, 0, VS), need1, L0, L1);
+        if (need0 || need1) row_L1(a, r, r + (int64_t)gridDim.x * PT, V(a, 0, VS), two ? V(a, 1, VS) : V(a, 0, VS), need1, L0, L1);
         for (int k = 0; k < a.ns; ++k) {
             T* x = k == 0 ? a.u : a.v;
             if (k == 0 ? e0 : e1) {
@@ -969,11 +1041,17 @@ __global__ void __launch_bounds__(PT, PT_MINB) phase_D(Args<T> a) {
 // E: x += alpha p + omega s ; r = s - omega t ; (r-hat, r), |r|^2; the last
 // block commits the iteration and decides whether the loop continues
 template <typename T>
-__global__ void __launch_bounds__(PV) phase_E(Args<T> a) {
+__device__ __forceinline__ void e_update(T alpha, T omega, T& x, T p, T s, T t, T& r) {
+    x = x + (alpha * p + omega * s);
+    r = s - omega * t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PV, PV_BPS) phase_E(Args<T> a) {
     PhaseCtl* c = a.ctl;
     typename PhaseAcc<T>::type d[4];
     for (auto& x : d) acc_zero(x);
-    const int64_t S = (int64_t)gridDim.x * PV;
+    const int64_t S = (int64_t)gridDim.x * PV, t0 = blockIdx.x * (int64_t)PV + threadIdx.x;
     for (int k = 0; k < a.ns; ++k) {
         if (!c->actE[k]) continue;
         const T alpha = (T)c->alpha_n[k], omega = (T)c->omega_n[k];
@@ -983,29 +1061,35 @@ __global__ void __launch_bounds__(PV) phase_E(Args<T> a) {
         const T* __restrict__ t = V(a, k, VT);
         const T* __restrict__ rh = V(a, k, VRH);
         T* __restrict__ r = V(a, k, VR);
-        for (int64_t i0 = blockIdx.x * (int64_t)PV + threadIdx.x; i0 < a.N; i0 += VUE * S) {
-            T xv[VUE], pv[VUE], s_[VUE], tv[VUE], hv[VUE];
+        int64_t i = t0;
+        if (a.vec4) {
+            const int64_t G = a.N >> 2;
+            for (int64_t g = t0; g < G; g += S) {
+                const int64_t e = 4 * g;
+                T xv[4], pv[4], s_[4], tv[4], hv[4], rn[4];
+                ld4v(x + e, xv);
+                ld4v(p + e, pv);
+                ld4v(sv + e, s_);
+                ld4v(t + e, tv);
+                ld4v(rh + e, hv);
 #pragma unroll
-            for (int u = 0; u < VUE; ++u) {
-                const int64_t i = i0 + u * S;
-                const bool in = i < a.N;
-                xv[u] = in ? x[i] : T(0);
-                pv[u] = in ? p[i] : T(0);
-                s_[u] = in ? sv[i] : T(0);
-                tv[u] = in ? t[i] : T(0);
-                hv[u] = in ? rh[i] : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < VUE; ++u) {
-                const int64_t i = i0 + u * S;
-                if (i < a.N) {
-                    x[i] = xv[u] + (alpha * pv[u] + omega * s_[u]);
-                    const T rn = s_[u] - omega * tv[u];
-                    r[i] = rn;
-                    acc_add(d[2 * k], hv[u], rn);
-                    acc_add(d[2 * k + 1], rn, rn);
+                for (int j = 0; j < 4; ++j) {
+                    e_update(alpha, omega, xv[j], pv[j], s_[j], tv[j], rn[j]);
+                    acc_add(d[2 * k], hv[j], rn[j]);
+                    acc_add(d[2 * k + 1], rn[j], rn[j]);
                 }
+                st4v(x + e, xv);
+                st4v(r + e, rn);
             }
+            i = 4 * G + t0;
+        }
+        for (; i < a.N; i += S) {
+            T xi = x[i], rn;
+            e_update(alpha, omega, xi, p[i], sv[i], t[i], rn);
+            x[i] = xi;
+            r[i] = rn;
+            acc_add(d[2 * k], rh[i], rn);
+            acc_add(d[2 * k + 1], rn, rn);
         }
     }
     if (phase_reduce<4, PV>(d, a.pp, c->totE, &c->ticket) && threadIdx.x == 0) {
@@ -1112,6 +1196,8 @@ void fill_args(Args<T>& a, rbffd_op* op, rbffd_state* s, const rbffd_step_params
     a.src_rate = p->source_rate;
     a.tstart = ws->tstart;
     a.vec = (T*)ws->vec;
+    a.ldv = (op->N + 3) & ~(int64_t)3;
+    a.vec4 = ((uintptr_t)s->u % 16 == 0 && (p->nspecies == 1 || (uintptr_t)s->v % 16 == 0)) ? 1 : 0;
     a.ns = p->nspecies;
     a.model = p->model;
     for (int i = 0; i < 8; ++i) a.c[i] = (T)p->coef[i];
@@ -1160,7 +1246,7 @@ rbffd_status launch_step(Args<T>& a, rbffd_step_ws* ws, cudaStream_t st) {
 template <typename T>
 void phase_grids(const Args<T>& a, unsigned* g_rows, unsigned* g_vec) {
     *g_rows = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.N + PT - 1) / PT, (int64_t)sm_count() * PT_MINB));
-    *g_vec = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.N + PV - 1) / PV, (int64_t)sm_count()));
+    *g_vec = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.N + PV - 1) / PV, (int64_t)sm_count() * PV_BPS));
 }
 
 // One step of the phase-kernel path from the host (no graph): R, then the
@@ -1371,7 +1457,7 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         const int64_t rows_per_block = ws->threads == 1024 ? 1024 : 4 * 256;
         int64_t want = (op->N + rows_per_block - 1) / rows_per_block;
         ws->blocks = (int)std::max<int64_t>(1, std::min(maxb, std::max<int64_t>(want, 1)));
-        RBFFD_CUDA_TRY(cudaMalloc(&ws->vec, 2 * 7 * op->N * elem));
+        RBFFD_CUDA_TRY(cudaMalloc(&ws->vec, 2 * 7 * ((op->N + 3) & ~(int64_t)3) * elem));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->partial, (size_t)NPHASE * ws->blocks * NSLOT * sizeof(double)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->bar, sizeof(unsigned long long)));
         RBFFD_CUDA_TRY(cudaMalloc(&ws->flags, 5 * sizeof(int)));
