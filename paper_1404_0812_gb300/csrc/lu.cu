@@ -20,8 +20,10 @@
 // applies the interchange and the rank-1 update to the window columns
 // c + 1 .. c + kl + ku that it owns (j mod blocks); the window (~kl (kl + ku)
 // elements) stays in L2.  The substitutions are sequential in the rows; one
-// 1024-thread block per species keeps the active window of the solution in
-// a shared-memory ring and streams the factor's columns in with cp.async,
+// 256-thread block per species keeps the active window of the solution in
+// a shared-memory ring and streams each factor column (with its multiplier,
+// diagonal and pivot) into a ring of D shared-memory slots by bulk copies
+// (cp.async.bulk, completing on one mbarrier per slot, every wait bounded),
 // D columns ahead, so each step costs one __syncthreads and a shared-memory
 // update of kl (forward) or kl + ku (back) entries.
 #include "common.cuh"
