@@ -55,12 +55,29 @@ __global__ void bbox_partial(const double* __restrict__ X, const double* __restr
     if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
 }
 
-__global__ void bbox_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
-    int a = threadIdx.x;
-    if (a >= 6) return;
-    double v = a < 3 ? INFINITY : -INFINITY;
-    for (int b = 0; b < nb; ++b) v = a < 3 ? fmin(v, part[b * 6 + a]) : fmax(v, part[b * 6 + a]);
-    out[a] = v;
+// one block: each thread folds a strided subset of the per-block partials,
+// then a shared-memory tree (min and max are exact: any order gives the
+// same box)
+__global__ void __launch_bounds__(BB_THREADS) bbox_final(const double* __restrict__ part, int nb,
+                                                        double* __restrict__ out) {
+    __shared__ double s[6][BB_THREADS];
+    double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nb; b += BB_THREADS)
+        for (int a = 0; a < 3; ++a) {
+            v[a] = fmin(v[a], part[b * 6 + a]);
+            v[3 + a] = fmax(v[3 + a], part[b * 6 + 3 + a]);
+        }
+    for (int a = 0; a < 6; ++a) s[a][threadIdx.x] = v[a];
+    __syncthreads();
+    for (int w = BB_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int a = 0; a < 3; ++a) {
+                s[a][threadIdx.x] = fmin(s[a][threadIdx.x], s[a][threadIdx.x + w]);
+                s[3 + a][threadIdx.x] = fmax(s[3 + a][threadIdx.x], s[3 + a][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
 struct Grid {
@@ -321,7 +338,7 @@ rbffd_status knn_stencils(rbffd_op* op, const double* nodes, const double* norma
     RBFFD_CUDA_TRY(cudaMemsetAsync(bb_d + 6, 0, sizeof(int), st));
     bbox_partial<<<nb, BB_THREADS, 0, st>>>(nodes, normals, N, part, reinterpret_cast<int*>(bb_d + 6));
     note_launch();
-    bbox_final<<<1, 32, 0, st>>>(part, nb, bb_d);
+    bbox_final<<<1, BB_THREADS, 0, st>>>(part, nb, bb_d);
     note_launch();
     RBFFD_CUDA_TRY(cudaGetLastError());
     double bb[7];

@@ -752,6 +752,8 @@ __device__ __forceinline__ void row_L1(const Args<T>& a, int64_t r, int64_t rnex
     y1 = two ? s1 : T(0);
 }
 
+constexpr int RED_ROUNDS = 4;   // rounds of partials the last block loads at once
+
 // K sums per block (each thread's accumulators, in float64 from here on)
 // into pp[block][0..K-1]; the last block of the grid sums them in block
 // order into tot[0..K-1] and returns true.  Blocks of NTB <= 1024 threads.
@@ -779,12 +781,23 @@ __device__ bool phase_reduce(const A (&v)[K], double* pp, double* tot, unsigned 
     if (!last) return false;
     __threadfence();
     // fixed order: thread t sums blocks t, t + NTB, ...; then a fixed tree
-    // over the threads' sums
+    // over the threads' sums.  The loads of the first RED_ROUNDS rounds go
+    // out together (one L2 round trip instead of one per round and sum)
     __shared__ double acc[K][NTB];
+    double part[K][RED_ROUNDS];
+#pragma unroll
+    for (int u = 0; u < RED_ROUNDS; ++u) {
+        const int64_t b = threadIdx.x + (int64_t)u * NTB;
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[k][u] = b < gridDim.x ? __ldcg(pp + b * 8 + k) : 0.0;
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         double t = 0.0;
-        for (int64_t b = threadIdx.x; b < gridDim.x; b += NTB) t += __ldcg(pp + b * 8 + k);
+#pragma unroll
+        for (int u = 0; u < RED_ROUNDS; ++u)
+            if (threadIdx.x + (int64_t)u * NTB < gridDim.x) t += part[k][u];
+        for (int64_t b = threadIdx.x + (int64_t)RED_ROUNDS * NTB; b < gridDim.x; b += NTB) t += __ldcg(pp + b * 8 + k);
         acc[k][threadIdx.x] = t;
     }
     __syncthreads();
