@@ -891,7 +891,10 @@ def run_ours(args):
     hW = torch.empty(elems, dtype=torch.float64).pin_memory()
     hE = torch.empty(N_NODES, dtype=torch.float64).pin_memory()
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    # one untimed round first (as the device-timed loop has its warm-up): the
+    # first host-to-device copies into fresh device tensors take new blocks
+    # from torch's allocator
+    for it in range(1 + max(1, min(args.steps, 3))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -904,7 +907,8 @@ def run_ours(args):
         hW.copy_(ell["w64"], non_blocking=True)
         hE.copy_(R.get_eps(op)[0], non_blocking=True)
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        if it > 0:
+            e2e_times.append(time.perf_counter() - t0)
     h2d = hX.numel() * 8 + hN.numel() * 8 + hP.numel() * 4
     d2h = hI.numel() * 4 + hW.numel() * 8 + hE.numel() * 8
     # the same step without the networks (the plain eps search), timed once
@@ -1034,6 +1038,7 @@ def run_ours(args):
         "other_configs": configs,
         "e2e": {"value": round(N_NODES / statistics.mean(e2e_times), 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": [round(t * 1e3, 3) for t in e2e_times], "warmup": 1,
                 "returned": "the built operator (sliced ELL: int32 indices + float64 weights) and eps"},
         "rates": {"learned_start_in_distribution": round(value, 1),
                   "plain_search_no_networks": round(N_NODES / (plain_step_ms * 1e-3), 1),
