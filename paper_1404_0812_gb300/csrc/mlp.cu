@@ -84,13 +84,22 @@ __global__ void features_kernel(const double* __restrict__ X, const double* __re
     double it = rsqrt(t1x * t1x + t1y * t1y + t1z * t1z);
     t1x *= it; t1y *= it; t1z *= it;
     double t2x = ny * t1z - nz * t1y, t2y = nz * t1x - nx * t1z, t2z = nx * t1y - ny * t1x;
+    // the projections in float32: each offset is formed in float64 (no
+    // cancellation) and rounded once, the frame vectors carry the 1 / r_s
+    // scale; the float32 features then differ from float64 projections by
+    // a few float32 roundings (~1e-7 of their size), and the float64 pipe
+    // (a small fraction of the float32 one here) does only the subtractions
+    const float f1x = (float)(t1x * irs), f1y = (float)(t1y * irs), f1z = (float)(t1z * irs);
+    const float f2x = (float)(t2x * irs), f2y = (float)(t2y * irs), f2z = (float)(t2z * irs);
+    const float f3x = (float)(nx * irs), f3y = (float)(ny * irs), f3z = (float)(nz * irs);
     float* f = feats + lr * (int64_t)(3 * n);
     for (int j = 0; j < n; ++j) {
         int k = idx[ell_elem(off, npad, lr, j)];
-        double dx = X[3 * (int64_t)k] - cx, dy = X[3 * (int64_t)k + 1] - cy, dz = X[3 * (int64_t)k + 2] - cz;
-        f[3 * j] = (float)((t1x * dx + t1y * dy + t1z * dz) * irs);
-        f[3 * j + 1] = (float)((t2x * dx + t2y * dy + t2z * dz) * irs);
-        f[3 * j + 2] = (float)((nx * dx + ny * dy + nz * dz) * irs);
+        const float dx = (float)(X[3 * (int64_t)k] - cx), dy = (float)(X[3 * (int64_t)k + 1] - cy),
+                    dz = (float)(X[3 * (int64_t)k + 2] - cz);
+        f[3 * j] = fmaf(f1x, dx, fmaf(f1y, dy, f1z * dz));
+        f[3 * j + 1] = fmaf(f2x, dx, fmaf(f2y, dy, f2z * dz));
+        f[3 * j + 2] = fmaf(f3x, dx, fmaf(f3y, dy, f3z * dz));
     }
     if (target) target[lr] = (float)log(eps[row_node[gi.row_begin[g] + lr]] * rs);
 }
