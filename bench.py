@@ -897,7 +897,7 @@ def run_ours(args):
     for it in range(1 + max(1, min(args.steps, 3))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
-        sev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        sev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         t0 = time.perf_counter()
         sev[0].record(stream)
         Xd = hX.to(dev, non_blocking=True)
@@ -908,14 +908,17 @@ def run_ours(args):
         sev[2].record(stream)
         e2e_phases.append(R.get_build_timings(op))
         ell = R.get_ell(op)
-        hI.copy_(ell["idx"], non_blocking=True)
-        hW.copy_(ell["w64"], non_blocking=True)
-        hE.copy_(R.get_eps(op)[0], non_blocking=True)
         sev[3].record(stream)
+        hI.copy_(ell["idx"], non_blocking=True)
+        sev[4].record(stream)
+        hW.copy_(ell["w64"], non_blocking=True)
+        sev[5].record(stream)
+        hE.copy_(R.get_eps(op)[0], non_blocking=True)
+        sev[6].record(stream)
         torch.cuda.synchronize()
         if it > 0:
             e2e_times.append(time.perf_counter() - t0)
-            e2e_split.append([sev[0].elapsed_time(sev[1]), sev[1].elapsed_time(sev[2]), sev[2].elapsed_time(sev[3])])
+            e2e_split.append([sev[i].elapsed_time(sev[i + 1]) for i in range(6)])
     h2d = hX.numel() * 8 + hN.numel() * 8 + hP.numel() * 4
     d2h = hI.numel() * 4 + hW.numel() * 8 + hE.numel() * 8
     # the same step without the networks (the plain eps search), timed once
@@ -1047,9 +1050,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": [round(t * 1e3, 3) for t in e2e_times], "warmup": 1,
                 "phases_ms": {k: round(statistics.mean(p[k] for p in e2e_phases[1:]), 3) for k in e2e_phases[0]},
-                "events_ms": {"h2d": round(statistics.mean(x[0] for x in e2e_split), 3),
-                              "build_and_step": round(statistics.mean(x[1] for x in e2e_split), 3),
-                              "d2h": round(statistics.mean(x[2] for x in e2e_split), 3)},
+                "events_ms": {k: round(statistics.mean(x[i] for x in e2e_split), 3) for i, k in enumerate(
+                    ("h2d", "build_and_step", "views", "d2h_idx", "d2h_w64", "eps"))},
                 "returned": "the built operator (sliced ELL: int32 indices + float64 weights) and eps"},
         "rates": {"learned_start_in_distribution": round(value, 1),
                   "plain_search_no_networks": round(N_NODES / (plain_step_ms * 1e-3), 1),
