@@ -779,6 +779,12 @@ def run_ours(args):
     nper = W.stencil_size_groups(n_nodes, SIZES)
     X, Nr, NP = T(ns.X), T(ns.normals), T(nper, torch.int32)
     nets = None if (args.no_learned or args.profile_plain) else train_networks(R, W, T, torch)
+    # hand back what the training left in torch's cache and the library's
+    # pool (their blocks fragment the device memory the timed builds allocate
+    # from); the warm-up steps map the build's scratch again
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    R.release_memory()
     s = W.SCHNAKENBERG
     name, coef = R.model_coefs(s)
     u0, v0 = W.schnakenberg_initial(n_nodes, seed=2)
