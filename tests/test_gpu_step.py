@@ -375,3 +375,38 @@ def test_phase_kernel_path_one_species_heat(R, sphere200k):
     assert rep["status"] == 0 and rep["max_iters_v"] == 0
     o = ostp.imex_run(lambda x: L @ x, u0, None, dict(model="none", dt=1e-4, delta_u=1.0), 30)
     assert rel_inf(st.u.cpu().numpy(), o["u"]) <= 1e-9
+
+
+def test_phase_kernel_path_ragged_and_unaligned(R):
+    """The phase kernels' vector phases move 16-byte groups when the state
+    is 16-byte aligned and take the last N mod 4 elements one by one; with
+    an unaligned state (a view one element into a buffer) they run element
+    by element.  N = 200,003 (N mod 4 = 3), float32 Schnakenberg, 10 SBDF2
+    steps: both layouts against the oracle's steps on the same operator
+    (1e-5), and against each other (1e-6: the same steps, dot products
+    summed in another order)."""
+    ns = W.fibonacci_sphere(200_003)
+    op = R.build_operator(T(ns.X), T(ns.normals), 31, kernel="imq",
+                          eps_override=T(np.full(ns.N, 2.5 * math.sqrt(ns.N / 2562.0))))
+    L = _csr_rows(R, op, ns.N)
+    s = W.SCHNAKENBERG
+    u0, v0 = W.schnakenberg_initial(ns.N, seed=6)
+    name, coef = R.model_coefs(s)
+    p = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
+                     delta_v=s["delta_v"], coef=coef, tol=1e-8, use_graph=True)
+    o = ostp.imex_run(lambda x: L @ x, u0, v0, s, 10)
+    out = []
+    for offset in (0, 1):
+        bu = torch.zeros(ns.N + 1, dtype=torch.float32, device="cuda")
+        bv = torch.zeros(ns.N + 1, dtype=torch.float32, device="cuda")
+        u, v = bu[offset:offset + ns.N], bv[offset:offset + ns.N]
+        u.copy_(T(u0, torch.float32))
+        v.copy_(T(v0, torch.float32))
+        assert (u.data_ptr() % 16 == 0) == (offset == 0)
+        st = R.StepState.create(u, v)
+        rep = R.step_imex(op, st, p, 10)
+        assert rep["status"] == 0
+        uu, vv = st.u.cpu().numpy().astype(np.float64), st.v.cpu().numpy().astype(np.float64)
+        assert rel_inf(uu, o["u"]) <= 1e-5 and rel_inf(vv, o["v"]) <= 1e-5
+        out.append((uu, vv))
+    assert rel_inf(out[0][0], out[1][0]) <= 1e-6 and rel_inf(out[0][1], out[1][1]) <= 1e-6
