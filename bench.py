@@ -76,6 +76,9 @@ def _parse():
     ap.add_argument("--profile", action="store_true", help="one small run for ncu (NVTX 'profiled')")
     ap.add_argument("--profile-n", type=int, default=40_000, help="nodes of the --profile case")
     ap.add_argument("--profile-plain", action="store_true", help="--profile without the learned start")
+    ap.add_argument("--profile-lu", action="store_true",
+                    help="the banded-LU direct solve for ncu: the RCM-ordered 40k torus (n = 50), the SBDF2 "
+                         "matrix factorised, 2 LU steps, then 1 step inside the NVTX range 'profiled'")
     ap.add_argument("--profile-step", action="store_true",
                     help="--profile of the IMEX step instead: after 4 graph-replayed steps, 3 steps with "
                          "the same kernels launched from the host inside the NVTX range 'profiled' "
@@ -812,6 +815,28 @@ def run_ours(args):
                "sphere2m_gray_scott": _c5_standin(R, W, T, torch, nets, steps=10_000, f64_steps=10_000)}
         out["wall_s"] = round(time.perf_counter() - t0, 1)
         print(json.dumps(out))
+        return
+
+    if args.profile_lu:
+        ns = W.torus_staggered(82)
+        op0 = R.build_operator(T(ns.X), T(ns.normals), 50, kernel="imq", kappa_target=KAPPA_T)
+        perm = R.rcm_order(op0).cpu().numpy()
+        del op0
+        opl = R.build_operator(T(ns.X[perm]), T(ns.normals[perm]), 50, kernel="imq", kappa_target=KAPPA_T)
+        R.release_memory()
+        s = W.SCHNAKENBERG
+        name, coef = R.model_coefs(s)
+        u0, v0 = W.schnakenberg_initial(ns.N, seed=2)
+        pl = R.StepParams(model=name, nspecies=2, dtype=torch.float32, dt=s["dt"], delta_u=s["delta_u"],
+                          delta_v=s["delta_v"], coef=coef, use_graph=False, solver="lu")
+        stl = R.StepState.create(T(u0[perm], torch.float32), T(v0[perm], torch.float32))
+        R.step_imex(opl, stl, pl, 2)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        R.step_imex(opl, stl, pl, 1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_case": "torus_40344_rcm_lu_step", "N": ns.N, "bandwidths": list(R.op_bandwidth(opl))}))
         return
 
     if args.profile and args.profile_step:
