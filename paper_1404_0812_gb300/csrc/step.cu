@@ -434,7 +434,8 @@ __device__ __forceinline__ void rhs_row(const Args<T>& a, const StepCoef<T>& kc,
 }
 
 // NT threads per block: 1024 (one block per SM, <= 64 registers) for large
-// operators, 256 for small ones
+// operators (there only the LU step's right-hand side runs here), 256 for
+// small ones
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) step_kernel(Args<T> a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1451,13 +1452,16 @@ extern "C" rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* s, const rbff
         op->step = ws;
         ws->elem = elem;
         ws->N = op->N;
-        // Large operators: one 1024-thread block per SM, so that only one
-        // block per SM meets at each grid barrier (1M-node operator: 2.67 ms
+        // The cooperative kernel's shape.  Large operators (a row per thread
+        // at one 1024-thread block per SM) run BiCGSTAB as phase kernels and
+        // use the cooperative launch only for the right-hand side of an LU
+        // step; there one 1024-thread block per SM meets at each grid barrier
+        // (measured when BiCGSTAB still ran in it, 1M-node operator: 2.67 ms
         // per step against 3.08 ms with 2 x 512 and 3.22 ms with 2 x 256
-        // threads per SM; 4 x 256 is slower still, 3.94 ms -- the barrier's
-        // cost grows with its blocks) once there is a row per thread.  Smaller
-        // ones keep 256-thread blocks (about four rows per thread) so that they
-        // still spread over the SMs.
+        // threads per SM; 4 x 256 was slower still, 3.94 ms -- the barrier's
+        // cost grows with its blocks).  Smaller operators keep 256-thread
+        // blocks (about four rows per thread) so that they still spread over
+        // the SMs.
         ws->threads = op->N >= (int64_t)1024 * sm_count() ? 1024 : 256;
         int dev = 0, per_sm = 0;
         RBFFD_CUDA_TRY(cudaGetDevice(&dev));
