@@ -160,7 +160,9 @@ typedef struct {
     int model;          /* reaction kinetics, see coef below */
     int nspecies;       /* 1 (u only, heat/forced diffusion) or 2 (u, v) */
     int dtype;          /* RBFFD_F32 or RBFFD_F64 state and arithmetic
-                           (dot products always accumulate in float64) */
+                           (float32 dot products accumulate in float64, or,
+                           for large operators, in compensated float32 --
+                           Ogita-Rump-Oishi Dot2 -- of the same accuracy) */
     double dt;          /* time step */
     double delta_u, delta_v;   /* diffusion coefficients */
     double coef[8];     /* LINEAR: lu, lv.  SCHNAKENBERG: a, b, gamma.
@@ -227,11 +229,16 @@ typedef struct {
  *                                    + 12 dt (4 f^n - 6 f^{n-1} + 4 f^{n-2} - f^{n-3})
  *                                    + 12 dt s(t^{n+1})
  * (s the optional source of params, zero without one),
- * each implicit system solved by BiCGSTAB from x0 = u^n (Section 4.2).
- * One cooperative persistent launch per step (optionally replayed from a
- * CUDA graph).  Synchronises the stream at the end and fills report (may be
+ * each implicit system solved by BiCGSTAB from x0 = u^n (Section 4.2), or
+ * by the banded LU factors (params->solver).  Operators with fewer than 1024
+ * rows per SM: one cooperative persistent launch per step; larger ones:
+ * BiCGSTAB as a sequence of kernels whose iteration loop runs on the device
+ * (a WHILE node of the CUDA graph, or, with use_graph = 0, the same kernels
+ * from a host loop).  Either path is replayed from a CUDA graph when
+ * use_graph = 1 (captured at the first call, again whenever an argument
+ * changes).  Synchronises the stream at the end and fills report (may be
  * NULL).  Returns RBFFD_SOLVER_NOT_CONVERGED (with report->failed_step) or
- * RBFFD_TIMEOUT when a bounded grid barrier gave up.
+ * RBFFD_TIMEOUT when a bounded wait gave up.
  */
 rbffd_status rbffd_step_imex(rbffd_op* op, rbffd_state* state, const rbffd_step_params* params,
                              int64_t nsteps, void* stream, rbffd_step_report* report);
